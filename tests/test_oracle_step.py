@@ -1,0 +1,351 @@
+"""Pins of the oracle's time step against what the paper and the mathematics fix.
+
+Each test would fail on a plausible slip in the oracle (dropped term, wrong sign,
+wrong index or weight, transposed operand):
+  - equilibrium / forcing moment identities (Eqs. Single_Phase_EDF, Guo_Forcing_Scheme);
+  - M^(1), M^(2) exact on quadratic psi; F^SC = -G psi grad psi on linear psi;
+  - the eps / kappa force terms against the divergence of Eq. New_Pressure_Tensor;
+  - mass conservation, momentum balance, Newton's third law of F^SC;
+  - shear-wave decay at nu = (tau - 1/2)/3, Poiseuille flow between bounce-back walls;
+  - MRT with all rates 1/tau is BGK; independence of G < 0;
+  - planar coexistence at the mechanical-stability densities and second-order
+    convergence to the App. A profile under diffusive refinement.
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle
+from oracle import params as pp
+from paper_2504_15018_gb300 import inputs
+
+PR = dict(kind="pr", a=2.0 / 49.0, b=2.0 / 21.0, R=1.0, omega=0.327)
+TC = pp.pr_Tc(PR["a"], PR["b"])
+
+
+def pr_eos(t_ratio):
+    return dict(PR, T=t_ratio * TC)
+
+
+# ------------------------------------------------------------------ local parts
+
+
+def test_d2q9_velocity_set_is_the_paper_order():
+    c, w = oracle.velocity_set(oracle.D2Q9)
+    expect = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    assert [tuple(v[:2]) for v in c] == expect
+    assert np.allclose(w, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, rtol=0, atol=1e-17)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_lattice_isotropy(lattice):
+    c, w = oracle.velocity_set(lattice)
+    d = 2 if lattice == oracle.D2Q9 else 3
+    c = c[:, :d].astype(float)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose(np.einsum("i,ia->a", w, c), 0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(d) / 3, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0, atol=1e-16)
+    I = np.eye(d)
+    fourth = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I) + np.einsum("ad,bc->abcd", I, I)) / 9
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), fourth, atol=1e-16)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_equilibrium_moments(lattice):
+    c, _ = oracle.velocity_set(lattice)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        rho = rng.uniform(0.05, 8.0)
+        u = rng.uniform(-0.1, 0.1, 3)
+        if lattice == oracle.D2Q9:
+            u[2] = 0.0
+        f = oracle.feq(lattice, rho, u)
+        assert f.sum() == pytest.approx(rho, rel=1e-14)
+        assert np.allclose(f @ c, rho * u, rtol=0, atol=1e-14 * rho)
+        d = 2 if lattice == oracle.D2Q9 else 3
+        cc = c[:, :d].astype(float)
+        Pi = np.einsum("i,ia,ib->ab", f, cc, cc)
+        assert np.allclose(Pi, rho * np.eye(d) / 3 + rho * np.outer(u[:d], u[:d]), atol=1e-14 * rho)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_guo_forcing_moments(lattice):
+    c, _ = oracle.velocity_set(lattice)
+    d = 2 if lattice == oracle.D2Q9 else 3
+    cc = c[:, :d].astype(float)
+    rng = np.random.default_rng(2)
+    for tau in (0.56, 1.0, 1.7):
+        F = rng.normal(size=3) * 1e-2
+        u = rng.uniform(-0.1, 0.1, 3)
+        if d == 2:
+            F[2] = u[2] = 0.0
+        Fi = oracle.guo(lattice, tau, F, u)
+        k = 1 - 1 / (2 * tau)
+        assert abs(Fi.sum()) < 1e-16
+        assert np.allclose(Fi @ cc, k * F[:d], atol=1e-16)
+        second = np.einsum("i,ia,ib->ab", Fi, cc, cc)
+        assert np.allclose(second, k * (np.outer(F[:d], u[:d]) + np.outer(u[:d], F[:d])), atol=1e-16)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_mrt_basis_orthogonal_with_conserved_rows(lattice):
+    M, Minv = oracle.mrt_matrix(lattice)
+    c, w = oracle.velocity_set(lattice)
+    G = M @ M.T
+    assert np.allclose(G, np.diag(np.diag(G)), atol=1e-12)
+    assert np.allclose(Minv @ M, np.eye(len(w)), atol=1e-13)
+    assert np.allclose(M[0], 1.0)
+    jrows = (3, 5) if lattice == oracle.D2Q9 else (3, 5, 7)
+    for a, r in enumerate(jrows):
+        assert np.allclose(M[r], c[:, a])
+
+
+def _grid_params(lattice, dims, **kw):
+    kw.setdefault("eos", pr_eos(0.8))
+    return oracle.make_params(lattice, dims, **kw)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_stencils_exact_on_quadratic_psi(lattice):
+    """M1 = grad psi and M2 = Hess psi exactly for quadratic psi (interior cells)."""
+    dims = (12, 12, 1) if lattice == oracle.D2Q9 else (10, 10, 10)
+    d = 2 if lattice == oracle.D2Q9 else 3
+    P = _grid_params(lattice, dims, eps=0.0, kappa=1.0)
+    x, y, z = inputs.grid_coords(dims)
+    X = np.stack([x, y, z])[:d]
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=d) * 0.1
+    H = rng.normal(size=(d, d)) * 0.01
+    H = H + H.T
+    psi = 1.0 + g @ X + 0.5 * np.einsum("an,ab,bn->n", X, H, X)
+    M1, M2, F = oracle.psi_moments(P, psi)
+    interior = np.all((X >= 1) & (X <= np.array(dims[:d])[:, None] - 2), axis=0)
+    grad = (g[:, None] + H @ X).T
+    assert np.allclose(M1[interior, :d], grad[interior], atol=1e-13)
+    assert np.allclose(M2[interior][:, :d, :d], np.broadcast_to(H, (interior.sum(), d, d)), atol=1e-13)
+    # F^SC = -G psi M1 = -G psi grad psi when eps = 0, kappa = 1 (Sec. II with omega = 3 w_i)
+    assert np.allclose(F[interior, :d], psi[interior, None] * grad[interior], atol=1e-13)
+
+
+def test_uniform_density_has_zero_force():
+    for lattice, dims in ((oracle.D2Q9, (8, 8, 1)), (oracle.D3Q19, (6, 6, 6))):
+        P = _grid_params(lattice, dims, kappa=1.7, eps=2.0)
+        f = oracle.init(P, np.full(np.prod(dims), 2.5))
+        M1, M2, F = oracle.force_field(P, f)
+        assert np.abs(F).max() < 1e-15 and np.abs(M1).max() < 1e-15
+
+
+def _pressure_tensor_force(d, eps, kappa, G):
+    """-div of (Eq. New_Pressure_Tensor at (eps, kappa)) - (at eps = 0, kappa = 1), symbolically."""
+    xs = sp.symbols("x0:%d" % d)
+    L = 64 if d == 2 else 40
+    k = 2 * sp.pi / L
+    if d == 2:
+        psi = 1 + sp.Rational(1, 5) * sp.sin(k * xs[0]) + sp.Rational(3, 20) * sp.cos(2 * k * xs[1] + sp.Rational(3, 10)) * sp.sin(k * xs[0])
+    else:
+        psi = 1 + sp.Rational(1, 5) * sp.sin(k * xs[0]) * sp.cos(k * xs[2]) + sp.Rational(3, 20) * sp.cos(k * xs[1] + sp.Rational(3, 10))
+    grad2 = sum(sp.diff(psi, v) ** 2 for v in xs)
+    lap = sum(sp.diff(psi, v, 2) for v in xs)
+    dP = [[0] * d for _ in range(d)]
+    for a in range(d):
+        for b in range(d):
+            iso = (-G / 8 * eps * grad2 - G / 6 * (kappa - 1) * psi * lap) if a == b else 0
+            dP[a][b] = iso + G / 6 * (kappa - 1) * psi * sp.diff(psi, xs[a], xs[b])
+    F = [-sum(sp.diff(dP[a][b], xs[b]) for b in range(d)) for a in range(d)]
+    return sp.lambdify(xs, psi, "numpy"), [sp.lambdify(xs, Fa, "numpy") for Fa in F], L
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("eps,kappa", [(2.0, 1.0), (0.0, 2.0), (2.0, 0.3)])
+def test_force_terms_follow_the_pressure_tensor(lattice, eps, kappa):
+    """The eps / kappa terms of F^int equal -d_b of the matching part of Eq. New_Pressure_Tensor
+    up to O(k^2) on a smooth psi field (the reading adopted for the eps coefficient)."""
+    d = 2 if lattice == oracle.D2Q9 else 3
+    G = -1.0
+    psi_f, F_f, L = _pressure_tensor_force(d, eps, kappa, G)
+    dims = (L, L, 1) if d == 2 else (L, L, L)
+    x, y, z = inputs.grid_coords(dims)
+    X = [x, y, z][:d]
+    psi = psi_f(*X) * np.ones_like(x)
+    base = oracle.psi_moments(_grid_params(lattice, dims, eps=0.0, kappa=1.0, G=G), psi)[2]
+    test = oracle.psi_moments(_grid_params(lattice, dims, eps=eps, kappa=kappa, G=G), psi)[2]
+    dF = (test - base)[:, :d]
+    ref = np.stack([Fa(*X) * np.ones_like(x) for Fa in F_f], axis=1)
+    scale = np.abs(ref).max()
+    assert np.abs(dF - ref).max() < 0.06 * scale
+    if eps != 0.0:
+        printed = oracle.psi_moments(_grid_params(lattice, dims, eps=eps, kappa=kappa, G=G, eps_printed=True), psi)[2]
+        assert np.abs((printed - base)[:, :d] - ref).max() > 0.3 * scale
+
+
+def test_force_independent_of_G():
+    """psi^2 ~ 1/G, so every force term scales with G/|G| (Eq. Interaction_Potential with G < 0)."""
+    dims = (16, 16, 1)
+    rv, rl, _ = pp.pr_maxwell(PR["a"], PR["b"], 1.0, PR["omega"], 0.8 * TC)
+    rho = inputs.droplet(dims, (8.0, 8.0), 4.0, rv, rl)
+    Fs = []
+    for G in (-1.0, -0.37, -5.0):
+        P = _grid_params(oracle.D2Q9, dims, G=G, kappa=1.3)
+        Fs.append(oracle.force_field(P, oracle.init(P, rho))[2])
+    assert np.allclose(Fs[0], Fs[1], atol=1e-13) and np.allclose(Fs[0], Fs[2], atol=1e-13)
+
+
+# --------------------------------------------------------------------- dynamics
+
+
+def _two_phase(lattice, dims, t_ratio=0.8, wall=False):
+    rv, rl, _ = pp.pr_maxwell(PR["a"], PR["b"], 1.0, PR["omega"], t_ratio * TC)
+    if lattice == oracle.D2Q9:
+        rho = inputs.droplet(dims, (dims[0] / 2, dims[1] / 2), dims[0] / 4, rv, rl)
+    else:
+        rho = inputs.droplet(dims, (dims[0] / 2, dims[1] / 2, dims[2] / 2), dims[0] / 4, rv, rl)
+    return rho
+
+
+@pytest.mark.parametrize("lattice,dims,wall,mrt", [
+    (oracle.D2Q9, (16, 16, 1), False, False), (oracle.D2Q9, (16, 16, 1), True, True),
+    (oracle.D3Q19, (10, 10, 10), False, True), (oracle.D3Q19, (10, 10, 10), True, False)])
+def test_mass_conservation(lattice, dims, wall, mrt):
+    rho = _two_phase(lattice, dims)
+    P = _grid_params(lattice, dims, wall_y=wall, mrt=mrt, rates=dict(s_e=1.2, s_eps=1.4, s_q=1.1, s_pi=1.3, s_m=1.5),
+                     fext=(1e-5, 0, 0))
+    f = oracle.init(P, rho)
+    g = oracle.run(P, f, 200)
+    assert abs(g.sum() - f.sum()) / f.sum() < 1e-13
+
+
+@pytest.mark.parametrize("lattice,dims,mrt", [(oracle.D2Q9, (16, 16, 1), False), (oracle.D3Q19, (10, 10, 10), True)])
+def test_momentum_balance_and_third_law(lattice, dims, mrt):
+    """Periodic grid: sum_x j(t+1) = sum_x j(t) + sum_x F(t); sum_x F^SC = 0 (eps = 0, kappa = 1)."""
+    c, _ = oracle.velocity_set(lattice)
+    rho = _two_phase(lattice, dims)
+    rng = np.random.default_rng(4)
+    u0 = rng.uniform(-0.01, 0.01, (3 if lattice else 2, rho.size))
+    P = _grid_params(lattice, dims, mrt=mrt, kappa=1.4, fext=(2e-5, -1e-5, 0.0),
+                     rates=dict(s_e=1.2, s_eps=1.4, s_q=1.1, s_pi=1.3, s_m=1.5))
+    f = oracle.run(P, oracle.init(P, rho, u0), 3)
+    F = oracle.force_field(P, f)[2]
+    g = oracle.run(P, f, 1)
+    dJ = (g @ c).sum(0) - (f @ c).sum(0)
+    assert np.allclose(dJ, F.sum(0), atol=1e-13)
+    Psc = _grid_params(lattice, dims, eps=0.0, kappa=1.0)
+    Fsc = oracle.force_field(Psc, f)[2]
+    assert np.abs(Fsc.sum(0)).max() < 1e-12 * np.abs(Fsc).sum()
+
+
+@pytest.mark.parametrize("lattice,mrt,tau", [(oracle.D2Q9, False, 0.8), (oracle.D2Q9, True, 0.7),
+                                             (oracle.D3Q19, True, 0.9), (oracle.D3Q19, False, 1.3)])
+def test_shear_wave_decay(lattice, mrt, tau):
+    """u_x = U sin(k y) on a uniform, stable liquid decays as exp(-nu k^2 t), nu = (tau - 1/2)/3
+    (the decay exponent converges at O(k^2); n = 64 keeps it within 0.3 %)."""
+    n = 64
+    dims = (1, n, 1)
+    P = _grid_params(lattice, dims, tau=tau, mrt=mrt, rates=dict(s_e=1.9, s_eps=0.7, s_q=1.6, s_pi=1.2, s_m=1.8))
+    y = np.arange(n)
+    k = 2 * np.pi / n
+    U = 1e-4
+    d = 2 if lattice == oracle.D2Q9 else 3
+    u0 = np.zeros((d, n))
+    u0[0] = U * np.sin(k * y)
+    nu = (tau - 0.5) / 3.0
+    steps = int(1.15 / (nu * k * k))
+    f = oracle.init(P, np.full(n, 7.5), u0)
+    _, u, _ = oracle.moments(P, oracle.run(P, f, steps))
+    amp = 2.0 / n * (u[0] * np.sin(k * y)).sum()
+    assert -math.log(amp / U) / (nu * k * k * steps) == pytest.approx(1.0, abs=3e-3)
+
+
+@pytest.mark.parametrize("H", [8, 16])
+def test_poiseuille_between_bounce_back_walls(H):
+    """Steady channel flow: constant second difference -F/(rho nu), near-zero velocity at y = -1/2."""
+    tau, F, rho0 = 1.0, 1e-6, 7.5
+    P = _grid_params(oracle.D2Q9, (1, H, 1), wall_y=True, tau=tau, fext=(F, 0.0, 0.0))
+    f = oracle.init(P, np.full(H, rho0))
+    g = oracle.run(P, f, 40 * H * H)
+    _, u, _ = oracle.moments(P, g)
+    ux = u[0]
+    nu = (tau - 0.5) / 3.0
+    second = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    assert np.allclose(second, -F / (rho0 * nu), rtol=1e-6)
+    y = np.arange(H)
+    ana = F / (2 * rho0 * nu) * (y + 0.5) * (H - 0.5 - y)
+    assert np.abs(ux - ana).max() < 0.5 / H ** 2 * ana.max()
+
+
+def test_mrt_with_uniform_rates_is_bgk():
+    for lattice, dims in ((oracle.D2Q9, (12, 12, 1)), (oracle.D3Q19, (8, 8, 8))):
+        rho = _two_phase(lattice, dims)
+        tau = 0.9
+        r = 1.0 / tau
+        Pb = _grid_params(lattice, dims, tau=tau, kappa=1.2, fext=(1e-5, 0, 0))
+        Pm = _grid_params(lattice, dims, tau=tau, kappa=1.2, fext=(1e-5, 0, 0), mrt=True,
+                          rates=dict(s_e=r, s_eps=r, s_q=r, s_pi=r, s_m=r))
+        f = oracle.init(Pb, rho)
+        a, b = oracle.run(Pb, f, 40), oracle.run(Pm, f, 40)
+        assert np.abs(a - b).max() < 1e-12
+
+
+def test_dynamics_independent_of_G():
+    dims = (16, 16, 1)
+    rho = _two_phase(oracle.D2Q9, dims)
+    P1 = _grid_params(oracle.D2Q9, dims, G=-1.0)
+    P2 = _grid_params(oracle.D2Q9, dims, G=-2.5)
+    f = oracle.init(P1, rho)
+    assert np.abs(oracle.run(P1, f, 100) - oracle.run(P2, f, 100)).max() < 1e-11
+
+
+def _planar_coexistence(eps, eps_printed=False, t_ratio=0.9, steps=12000):
+    rv, rl, _ = pp.pr_maxwell(PR["a"], PR["b"], 1.0, PR["omega"], t_ratio * TC)
+    dims = (1, 128, 1)
+    rho = inputs.slab(dims, 1, 32, 96, rl, rv, 4.0)
+    P = _grid_params(oracle.D2Q9, dims, eos=pr_eos(t_ratio), eps=eps, eps_printed=eps_printed)
+    r, _, _ = oracle.moments(P, oracle.run(P, oracle.init(P, rho), steps))
+    return r[:16].mean(), r[48:80].mean()
+
+
+def test_planar_coexistence_follows_mechanical_stability():
+    """Sec. IV: the bulk densities of a relaxed planar interface satisfy the mechanical-stability
+    condition with the actual psi; eps = 2 under the adopted reading."""
+    T = 0.9 * TC
+    ps = lambda r: pp.pr_pressure(r, PR["a"], PR["b"], 1.0, PR["omega"], T)
+    mv, ml, _ = pp.mechanical_stability(ps, -1.0, 2.0, rho_max=0.999 / PR["b"])
+    rv, rl = _planar_coexistence(2.0)
+    assert rv == pytest.approx(mv, rel=0.015) and rl == pytest.approx(ml, rel=2e-3)
+    m0v, m0l, _ = pp.mechanical_stability(ps, -1.0, 0.0, rho_max=0.999 / PR["b"])
+    rv0, rl0 = _planar_coexistence(0.0)
+    assert rv0 == pytest.approx(m0v, rel=0.01) and rl0 == pytest.approx(m0l, rel=2e-3)
+
+
+def test_printed_eps_coefficient_acts_as_minus_half_eps():
+    """Documents the reading: with the coefficient exactly as printed in Eq. interactionForce,
+    input eps = -4 produces the coexistence of mechanical-stability exponent +2."""
+    T = 0.9 * TC
+    ps = lambda r: pp.pr_pressure(r, PR["a"], PR["b"], 1.0, PR["omega"], T)
+    mv, ml, _ = pp.mechanical_stability(ps, -1.0, 2.0, rho_max=0.999 / PR["b"])
+    rv, rl = _planar_coexistence(-4.0, eps_printed=True)
+    assert rv == pytest.approx(mv, rel=0.015) and rl == pytest.approx(ml, rel=2e-3)
+
+
+def test_planar_profile_converges_second_order_to_appendix_a():
+    """Sec. VI.A / App. A: paper EOS, xi = 1.5 k, Delta t ~ Delta x^2 (P ~ 1/k^2); the density
+    profile converges to the analytic one at second order (tau = 1 to reach equilibrium quickly)."""
+    errs = []
+    for k in (1, 2, 3):
+        conv = pp.si_converter(rho_v_phs=37.5, rho_l_phs=1187.0, nu_v_phs=0.339e-6, nu_l_phs=0.158e-6,
+                               gamma_phs=7.58e-3, L_phs=10e-6, L_lat=100 * k, tau_l=0.56, rho_l_lat=1.187,
+                               xi_lat=1.5 * k)
+        rv, rl, P = conv["rho_v"], conv["rho_l"], conv["P"]
+        nx = 60 * k
+        x = np.arange(nx, dtype=float)
+        rho = np.where(x < 30 * k, pp.planar_profile(x, 15 * k - 0.5, P, rv, rl),
+                       pp.planar_profile(-x, -(45 * k - 0.5), P, rv, rl))
+        Pp = oracle.make_params(oracle.D2Q9, (nx, 1, 1), eos=dict(kind="paper", rho_v=rv, rho_l=rl, P=P),
+                                tau=1.0, kappa=conv["kappa"], eps=2.0)
+        r, u, _ = oracle.moments(Pp, oracle.run(Pp, oracle.init(Pp, rho), 4000 * k * k))
+        assert np.abs(u).max() < 1e-5
+        errs.append(np.sqrt(((r - rho) ** 2).sum() / (rho ** 2).sum()))
+    orders = [math.log(errs[0] / errs[1]) / math.log(2), math.log(errs[1] / errs[2]) / math.log(1.5)]
+    assert min(orders) > 1.9, (errs, orders)
