@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Throughput of the P-LBM time step on GB300 (GLUPS and fraction of the HBM roofline).
+
+Default workload: D3Q19 two-phase flow between parallel plates, 512 x 256 x 256 cells,
+halfway bounce-back walls bounding y, periodic in x and z, liquid layers next to both
+walls and a vapour core (flat interfaces at y = 63.5 and 191.5), body force 1e-7 along x,
+Peng-Robinson EOS at T/Tc = 0.8, MRT collision, FP32 population storage.  Synthetic
+seeded input; the populations (2.5 GB) are larger than L2, so no flush is needed.
+
+One step = psi pass + fused force/collide/stream pass over the whole lattice.
+Multi-GPU: independent replicas (the workload does not exchange data across GPUs),
+weak scaling; value = cells * steps summed over ranks / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16s|fp64]
+                  [--collision mrt|bgk] [--dims 512x256x256] [--impl reference] [--no-variants]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P-LBM GLUPS and % HBM roofline, FP32/FP16 vs FP64 at matched Laplace error"
+PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
+POP_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
+PSI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16 storage / f32 arithmetic"}
+T_RATIO, BODY_FORCE = 0.8, 1e-7
+MRT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--precision", default="fp32", choices=list(PREC))
+    ap.add_argument("--collision", default="mrt", choices=["mrt", "bgk"])
+    ap.add_argument("--dims", default="512x256x256")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(dims, precision, collision):
+    return f"d3q19_plates_{dims[0]}x{dims[1]}x{dims[2]}_{precision}_{collision}_pr0.8"
+
+
+def bytes_per_cell(precision, q=19):
+    """Algorithmic bytes per cell update of the two-pass step: psi pass reads Q
+    populations and writes psi; the fused pass reads Q populations and psi, writes Q."""
+    sp, sq = POP_BYTES[precision], PSI_BYTES[precision]
+    return dict(psi_pass=q * sp + sq, fused_pass=2 * q * sp + sq, step=3 * q * sp + 2 * sq)
+
+
+def initial_density(dims, rho_v, rho_l):
+    from paper_2504_15018_gb300 import inputs
+    return inputs.plates_d3q19(dims, rho_v, rho_l)[1]
+
+
+def make_lattice(dims, precision, collision):
+    import paper_2504_15018_gb300 as plb
+    eos = plb.pr_eos(T_RATIO)
+    opts = plb.make_opts(precision=PREC[precision], collision=plb.PLB_MRT if collision == "mrt" else plb.PLB_BGK,
+                         wall_y=1, body_force=(BODY_FORCE, 0.0, 0.0), **MRT_RATES)
+    return plb.Lattice(plb.PLB_D3Q19, dims, eos, tau=1.0, G=-1.0, eps=2.0, opts=opts)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([float(r[1]) for r in rows])
+        smax = float(rows[0][2])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = sm[sm >= np.median(sm) * 0.5] if len(sm) else sm
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_15018_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per fused-pass launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    sha = re.search(r"kernel_source_sha:\s*(\w+)", text)
+    if not sha or sha.group(1) != kernel_source_sha():
+        return None
+    m = re.search(re.escape(workload) + r"\s*\|\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def time_steps(lat, steps, torch):
+    """Device time of `steps` steps with CUDA events on the lattice's stream."""
+    st = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    lat.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2504_15018_gb300 as plb
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dims = tuple(int(v) for v in args.dims.split("x"))
+    ncell = dims[0] * dims[1] * dims[2]
+    rho_v, rho_l, _ = plb.plb_solve_params(plb.pr_eos(T_RATIO))
+    rho0 = initial_density(dims, rho_v, rho_l)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    lat = make_lattice(dims, args.precision, args.collision)
+    lat.init(rho0)
+    lat.step(max(args.warmup, 3))
+    lat.status()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    t = time_steps(lat, args.steps, torch)
+    barrier()
+    clocks = sampler.stop()
+    lat.status()
+    if world > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * ncell * args.steps / t / 1e9
+
+    # roofline of the dominant kernel (fused pass), per-launch events on the same stream
+    nprof = min(args.steps, 20)
+    ms_psi, ms_fused = lat.step_timed(nprof)
+    bpc = bytes_per_cell(args.precision)
+    fused_gbs = bpc["fused_pass"] * ncell * nprof / (ms_fused / 1e3) / 1e9
+    psi_gbs = bpc["psi_pass"] * ncell * nprof / (ms_psi / 1e3) / 1e9
+    peak, peak_kind = peak_hbm()
+    wl = workload_name(dims, args.precision, args.collision)
+    traffic = recorded_traffic(wl)
+    roofline = {"bound": "hbm", "kernel": "k_collide (fused force + collide + stream)",
+                "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(fused_gbs / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": bpc["fused_pass"] * ncell,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "psi_pass_gbs": round(psi_gbs, 1), "psi_pass_frac": round(psi_gbs / peak, 4),
+                "step_gbs": round(value / world * bpc["step"], 1),
+                "step_frac": round(value / world * bpc["step"] / peak, 4),
+                "time_share_fused": round(ms_fused / (ms_fused + ms_psi), 3)}
+
+    # e2e through the public API with pinned host buffers: upload rho0, run, read fields back
+    e2e = None
+    if not args.no_e2e:
+        rho_pin = torch.from_numpy(rho0).pin_memory()
+        out_rho = torch.empty(ncell, dtype=torch.float64).pin_memory()
+        out_u = torch.empty(3 * ncell, dtype=torch.float64).pin_memory()
+        out_p = torch.empty(ncell, dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        plb.plb_init(lat.h, rho_pin)
+        lat.step(args.steps)
+        mass = lat.reduce(plb.PLB_MASS)[0]
+        plb.plb_moments(lat.h, out_rho, out_u, out_p)
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        h2d = rho_pin.numel() * 8
+        d2h = (out_rho.numel() + out_u.numel() + out_p.numel()) * 8 + 8
+        e2e = {"value": round(world * ncell * args.steps / te / 1e9, 4), "unit": "GLUPS",
+               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+               "what": "plb_init from pinned host rho0 + K steps + plb_reduce(mass) + plb_moments to pinned host",
+               "mass": mass}
+    del lat
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants:
+        for prec in ("fp16s", "fp64", "fp32"):
+            if prec == args.precision:
+                continue
+            lv = make_lattice(dims, prec, args.collision)
+            lv.init(rho0)
+            lv.step(3)
+            nst = 20 if prec != "fp64" else 6
+            tv = time_steps(lv, nst, torch)
+            lv.status()
+            g = ncell * nst / tv / 1e9
+            ms_p, ms_f = lv.step_timed(min(nst, 6))
+            bpv = bytes_per_cell(prec)
+            variants[prec] = {"glups": round(g, 3), "step_frac_hbm": round(g * bpv["step"] / peak, 4),
+                              "fused_frac_hbm": round(bpv["fused_pass"] * ncell * min(nst, 6) / (ms_f / 1e3) / 1e9 / peak, 4)}
+            del lv
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args, seconds=12.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": round(t / args.steps * 1e3, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+                "data": "synthetic (seeded tanh liquid-vapour layers, Maxwell densities of the PR EOS)",
+                "config": {"workload": wl, "cells": ncell, "lattice": "D3Q19", "collision": args.collision,
+                           "precision": args.precision, "eos": "Peng-Robinson a=2/49 b=2/21 w=0.327 T/Tc=0.8",
+                           "boundaries": "halfway bounce-back walls in y, periodic x and z",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * POP_BYTES[args.precision] * ncell / 1e9)},
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "cpu_baseline": cpu, "variants": variants or None}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def oracle_sample_setup(dims_full, precision, collision, ny_sample=16, nz_sample=16):
+    """Bounded sample of the plates workload for the FP64 oracle: a slab of the full
+    x extent with ny_sample rows between the walls and nz_sample planes."""
+    import oracle
+    from oracle import params as pp
+    a, b, om = 2.0 / 49.0, 2.0 / 21.0, 0.327
+    T = T_RATIO * pp.pr_Tc(a, b)
+    rv, rl, _ = pp.pr_maxwell(a, b, 1.0, om, T)
+    dims = (dims_full[0], ny_sample, nz_sample)
+    rho = initial_density(dims, rv, rl)
+    P = oracle.make_params(oracle.D3Q19, dims, wall_y=True, eos=dict(kind="pr", a=a, b=b, R=1.0, omega=om, T=T),
+                           tau=1.0, mrt=collision == "mrt", rates=MRT_RATES, fext=(BODY_FORCE, 0.0, 0.0))
+    return P, oracle.init(P, rho), dims
+
+
+def cpu_baseline_sample(args, seconds=12.0):
+    import oracle
+    dims_full = tuple(int(v) for v in args.dims.split("x"))
+    P, f, dims = oracle_sample_setup(dims_full, args.precision, args.collision)
+    n = dims[0] * dims[1] * dims[2]
+    t0 = time.perf_counter()
+    f = oracle.run(P, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(2, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.run(P, f, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n * steps / dt / 1e9, 6), "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 C oracle, D3Q19 {args.collision.upper()}, {dims[0]}x{dims[1]}x{dims[2]} slab of the "
+                      f"plates workload (walls in y), {steps} steps, {dt:.1f} s, OpenMP over cells"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    dims_full = tuple(int(v) for v in args.dims.split("x"))
+    P, f, dims = oracle_sample_setup(dims_full, args.precision, args.collision)
+    n = dims[0] * dims[1] * dims[2]
+    for _ in range(max(args.warmup, 3)):
+        f = oracle.run(P, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(P, f, 1)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    wl = workload_name(dims_full, args.precision, args.collision)
+    sample = (f"FP64 C oracle on the host cores, D3Q19 {args.collision.upper()}, one step of a "
+              f"{dims[0]}x{dims[1]}x{dims[2]} slab of the plates workload per timed step")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl, "cells_per_step": n, "sample": sample},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * plb.h -- C ABI of a GB300 (sm_103a) implementation of the per-time-step update
+ * of the pseudo-potential lattice Boltzmann method (P-LBM) of
+ * "On the consistency of pseudo-potential lattice Boltzmann methods"
+ * (Czelusniak, Bingert, Krause, Simonis; arXiv 2504.15018).
+ *
+ * One time step (Sec. II, Eq. LBE) on a D2Q9 or D3Q19 lattice, lattice units
+ * Delta x = Delta t = 1:
+ *   rho = sum_i f_i                                   (Eq. Density)
+ *   psi = sqrt(2 (p_EOS(rho) - rho/3) / G)            (Eq. Interaction_Potential)
+ *   M1_a = sum_i w_i psi(x+c_i) c_ia / c_s^2,
+ *   M2_ab = sum_i w_i psi(x+c_i) (c_ia c_ib - c_s^2 d_ab) / c_s^4   (Sec. II)
+ *   F = -G psi M1 + eps/kappa terms + F_ext            (Eqs. Shan_Chen_Force, interactionForce)
+ *   u = (sum_i f_i c_i + F/2) / rho                    (Eq. Momentum)
+ *   f_i* = f_i - (f_i - f_i^eq)/tau + F_i'             (Eqs. LBE, Single_Phase_EDF, Guo_Forcing_Scheme)
+ *          or the MRT generalisation (same Guo term in moment space)
+ *   f_i(x + c_i, t + 1) = f_i*(x, t)                   (streaming; halfway bounce-back at walls)
+ *
+ * eps term: Eq. interactionForce as printed contradicts Eq. New_Pressure_Tensor and the
+ * Maxwell rule at eps = 2 (Sec. IV); this library uses the coefficient that realises the
+ * printed pressure tensor: -G/12 (2 kappa - 2 - 3 eps) M1_b M2_ab + G/6 (kappa - 1) M1_a M2_bb.
+ *
+ * Conventions (all entry points):
+ *   - Cell index s = x + nx * (y + ny * z), x fastest.  D2Q9 uses nz = 1.
+ *   - Host arrays are FP64 whatever the storage precision.  Velocity fields are
+ *     stored component-major: u[a * N + s].  Population arrays exchanged with the
+ *     host are FP64, direction-major: f[i * N + s], directions in the order
+ *     reported by plb_velocity_set().
+ *   - Every function returns a PLB_* status; no exception crosses the ABI.
+ *     plb_last_error() gives a message for the last failure on the calling thread.
+ *   - The caller owns the device workspace and the CUDA stream; the library never
+ *     allocates device memory.  A handle is not thread-safe; use one stream per handle.
+ *   - Device work is enqueued on the handle's stream.  Functions that return host
+ *     data (plb_moments, plb_reduce, plb_get_*, plb_status) synchronise that stream.
+ */
+#ifndef PLB_H
+#define PLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    PLB_OK = 0,
+    PLB_EINVAL = 1,        /* invalid argument */
+    PLB_ENOMEM = 2,        /* workspace or host buffer too small */
+    PLB_ECUDA = 3,         /* CUDA runtime error (message in plb_last_error) */
+    PLB_ENONFINITE = 4,    /* a density became non-positive or non-finite */
+    PLB_EPSI_DOMAIN = 5,   /* 2 (p_EOS - rho/3) / G < 0 somewhere: psi undefined */
+    PLB_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    PLB_EUNSUPPORTED = 7   /* combination not built */
+};
+
+enum { PLB_D2Q9 = 0, PLB_D3Q19 = 1 };
+enum { PLB_EOS_PR = 0, PLB_EOS_PAPER = 1 };
+enum { PLB_FP64 = 0, PLB_FP32 = 1, PLB_FP16S = 2 };
+enum { PLB_BGK = 0, PLB_MRT = 1 };
+
+/* quantities of plb_reduce */
+enum {
+    PLB_MASS = 0,       /* sum rho                                  -> out[0]     */
+    PLB_MOMENTUM = 1,   /* sum rho u (u with the F/2 shift)         -> out[0..2]  */
+    PLB_UMAX = 2,       /* max |u|            (L_inf of Eq. norms)  -> out[0]     */
+    PLB_UL1 = 3,        /* sum |u|            (L_1 of Eq. norms)    -> out[0]     */
+    PLB_UL2 = 4,        /* sqrt(sum |u|^2)    (L_2 of Eq. norms)    -> out[0]     */
+    PLB_MEAN_RHO = 5,   /* mean rho over the box                    -> out[0]     */
+    PLB_MEAN_P = 6      /* mean p_scale p_EOS(rho) over the box     -> out[0]     */
+};
+
+/* Equation of state.
+ * PLB_EOS_PR: Peng-Robinson in lattice units (not in the paper; the usual choice of
+ *   pseudo-potential benchmarks): p = rho R T/(1 - b rho) - a alpha(T) rho^2/(1 + 2 b rho - b^2 rho^2),
+ *   alpha = [1 + (0.37464 + 1.54226 w - 0.26992 w^2)(1 - sqrt(T/Tc))]^2, Tc = 0.0778 a/(0.45724 b R).
+ * PLB_EOS_PAPER: Eq. EOS of Sec. IV with rho_v, rho_l and P = p_c / rho_c^3.
+ * p_scale multiplies p_EOS (the Delta t^2/Delta x^2 factor of Eq. Interaction_Potential;
+ *   1 in lattice units at r = 1). */
+typedef struct plb_eos_params {
+    int kind;
+    double a, b, R, omega, T_over_Tc;
+    double rho_v, rho_l, pc_over_rhoc3;
+    double p_scale;
+} plb_eos_params;
+
+/* Per-lattice options.  plb_default_opts() fills the defaults given in brackets. */
+typedef struct plb_opts {
+    double kappa;            /* surface-tension parameter of Eq. interactionForce [1] */
+    double tau_v;            /* <= 0: constant tau; else tau(rho) = tau_v + w (tau_l - tau_v),
+                                w = clamp((rho - tau_rho_v)/(tau_rho_l - tau_rho_v), 0, 1) (Sec. VI) [0] */
+    double tau_rho_v, tau_rho_l;   /* densities of the tau interpolation [coexistence densities] */
+    int collision;           /* PLB_BGK or PLB_MRT [PLB_BGK] */
+    double s_e, s_eps, s_q, s_pi, s_m;  /* MRT rates of the energy, energy-square, heat-flux,
+                                           and (D3Q19) pi and m moments; stress moments use 1/tau [1] */
+    int precision;           /* storage precision of the populations [PLB_FP32] */
+    double rho_ref;          /* PLB_FP16S stores f_i - w_i rho_ref; <= 0 picks the vapour
+                                coexistence density of the EOS [0] */
+    int wall_y;              /* 1: halfway bounce-back walls at y = -1/2 and y = ny - 1/2;
+                                psi on the wall equals psi of the adjacent fluid row [0 = periodic] */
+    double body_force[3];    /* external force density F_ext added to F (Sec. II) [0] */
+} plb_opts;
+
+typedef struct plb_state plb_t;
+
+/* Fills *opts with the defaults listed above. */
+void plb_default_opts(plb_opts *opts);
+
+/* Directions of the lattice in the library's order: c[3*i + a] and w[i]
+ * (Eq. VelocitySet for D2Q9; standard D3Q19).  Opposite directions are adjacent:
+ * opp(i) = i + 1 for odd i.  Returns Q (9 or 19), or -1 for an unknown lattice. */
+int plb_velocity_set(int lattice, int *c, double *w);
+
+/* Bytes of device workspace plb_create needs for this lattice, size and options
+ * (populations in one copy, padded psi field, reduction partials, staging, flags).
+ * Returns 0 on invalid arguments. */
+size_t plb_workspace_bytes(int lattice, const int dims[3], const plb_opts *opts);
+
+/* Creates a lattice.  dims = {nx, ny, nz} (nz = 1 for D2Q9).  tau = tau_l (> 1/2);
+ * G < 0 (any negative value gives the same dynamics, Eq. Interaction_Potential);
+ * eps: mechanical-stability exponent of Sec. IV (2 = Maxwell rule).
+ * dev_workspace: caller-owned device memory of at least plb_workspace_bytes(...) bytes,
+ * 256-byte aligned; it must outlive the handle.  cuda_stream: a cudaStream_t (NULL = default).
+ * opts may be NULL (defaults).  Errors: PLB_EINVAL, PLB_ENOMEM (workspace too small),
+ * PLB_EUNSUPPORTED, PLB_ECUDA. */
+int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
+               const plb_opts *opts, void *dev_workspace, size_t ws_bytes, void *cuda_stream, plb_t **out);
+
+/* Frees the handle (host memory only). */
+void plb_destroy(plb_t *h);
+
+/* f_i = f_i^eq(rho0, u0) (Eq. Single_Phase_EDF) on every cell; time reset to 0.
+ * rho0: host FP64 [N]; u0: host FP64 [d * N] or NULL (u = 0).  Pinned host memory makes
+ * the copies asynchronous.  Errors: PLB_EINVAL (non-positive / non-finite rho0), PLB_ECUDA. */
+int plb_init(plb_t *h, const double *rho0, const double *u0);
+
+/* Advances n time steps (two kernels per step: psi pass, then the fused force +
+ * collide + stream pass).  Asynchronous; returns launch errors only.  Device-side
+ * faults of the method (psi domain, non-finite density) are recorded in a device flag
+ * and reported by plb_status / plb_moments / plb_reduce. */
+int plb_step(plb_t *h, int n);
+
+/* Same as plb_step(h, n), with CUDA events recorded on the handle's stream around every
+ * launch; ms[0] receives the summed duration of the n psi passes, ms[1] of the n fused
+ * force + collide + stream passes (milliseconds).  Synchronises.  For measurement. */
+int plb_step_timed(plb_t *h, int n, double ms[2]);
+
+/* Synchronises the stream and returns PLB_EPSI_DOMAIN / PLB_ENONFINITE if a kernel
+ * met such a cell since creation or the last plb_init, else PLB_OK. */
+int plb_status(plb_t *h);
+
+/* Number of steps since plb_init. */
+long long plb_time(const plb_t *h);
+
+/* Macroscopic fields of the current state: rho (Eq. Density), u with the F/2 shift
+ * (Eq. Momentum), p = p_scale p_EOS(rho).  Host FP64 outputs, each may be NULL:
+ * rho [N], u [d * N], p [N].  Synchronises. */
+int plb_moments(plb_t *h, double *rho, double *u, double *p);
+
+/* A reduction over the box lo <= (x, y, z) < hi (NULL = whole lattice), summed in
+ * FP64 in a fixed order (deterministic).  out receives 1 value (3 for PLB_MOMENTUM).
+ * Synchronises. */
+int plb_reduce(plb_t *h, int what, const int lo[3], const int hi[3], double *out);
+
+/* Current populations f_i(x, t) (pre-collision) as host FP64 [Q * N], direction-major. */
+int plb_get_populations(plb_t *h, double *f);
+
+/* Replaces the populations (host FP64 [Q * N]); keeps the step counter. */
+int plb_set_populations(plb_t *h, const double *f);
+
+/* Raw checkpoint of the population store and the step counter (bit-exact restart).
+ * plb_state_bytes gives the size; get/set return PLB_ENOMEM if bytes is too small. */
+size_t plb_state_bytes(const plb_t *h);
+int plb_get_state(plb_t *h, void *host_buf, size_t bytes);
+int plb_set_state(plb_t *h, const void *host_buf, size_t bytes);
+
+/* Host FP64 parameter solve (Sec. IV): coexistence densities of the EOS by the
+ * equal-area (Maxwell) rule, and the coexistence pressure p0 (p_scale = 1).
+ * For PLB_EOS_PAPER these are rho_v, rho_l by construction. */
+int plb_solve_params(const plb_eos_params *eos, double *rho_v, double *rho_l, double *p0);
+
+/* Multiphase SI unit converter of Sec. V (Eqs. unit, unit2) plus the parameter
+ * formulas of Sec. IV (Eqs. thickness, surface_tension, r = 1).
+ * si = {rho_v, rho_l, nu_v, nu_l, gamma, L} (kg/m^3, m^2/s, N/m, m);
+ * lat = {L, tau_l, rho_l}; xi = interface width in lattice units.
+ * out = {C_L, C_T, C_M, C_U, C_VF, C_gamma, rho_v, tau_v, gamma_lat, pc_over_rhoc3, kappa}. */
+int plb_si_convert(const double si[6], const double lat[3], double xi, double out[11]);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *plb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLB_H */

@@ -1,0 +1,33 @@
+// Internal host-side declarations shared by the runtime and the parameter solve.
+#pragma once
+#include <cstddef>
+
+#include "plb.h"
+
+namespace plb {
+
+struct PrConstants {
+    double Tc, alpha, RT, aalpha;
+};
+
+PrConstants pr_constants(const plb_eos_params &e);
+double eos_pressure_host(const plb_eos_params &e, double rho);
+int solve_coexistence(const plb_eos_params &e, double &rho_v, double &rho_l, double &p0);
+int si_convert(const double si[6], const double lat[3], double xi, double out[11]);
+
+// Byte layout of the caller's device workspace (every region 256-byte aligned).
+struct Layout {
+    int Q, D;
+    long long n;            // cells
+    long long pstride;      // elements per population plane
+    int s_pop, s_psi;       // bytes per stored population / psi value
+    int gx, px, py, pz;     // psi padding and padded extents
+    long long psi_elems;
+    long long chunk;        // cells per staging chunk
+    int max_blocks;         // reduction partial blocks
+    size_t off_pops, off_psi, off_partials, off_out, off_staging, off_flags, total;
+};
+
+bool make_layout(int lattice, const int dims[3], int precision, Layout &L);
+
+}  // namespace plb

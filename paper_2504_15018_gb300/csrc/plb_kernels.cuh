@@ -1,0 +1,247 @@
+// Readout kernels (init, moments, population exchange, reductions) and the launcher
+// table of the step kernels (plb_step.cuh), templated over lattice and storage.
+// Instantiated once per storage precision (plb_kern_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "plb_device.cuh"
+#include "plb_launch.h"
+#include "plb_step.cuh"
+
+namespace plb {
+
+// Linear thread -> cell mapping (x fastest) for the readout kernels.
+__device__ __forceinline__ bool cell_coords(const KParams &p, long long s, int &x, int &y, int &z) {
+    if (s >= p.n) return false;
+    const long long plane = (long long)p.nx * p.ny;
+    z = (int)(s / plane);
+    const long long r = s - (long long)z * plane;
+    y = (int)(r / p.nx);
+    x = (int)(r - (long long)y * p.nx);
+    return true;
+}
+
+// ------------------------------------------------------------ init (a1)
+// f_i = f_i^eq(rho0, u0) in natural layout, for cells [c0, c0 + cn).
+template <class L, class S>
+__global__ void k_init(KParams p, S *__restrict__ A, const double *__restrict__ rho0, const double *__restrict__ u0,
+                       long long c0, long long cn, int has_u) {
+    using T = typename Store<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cn) return;
+    const long long s = c0 + k;
+    const T rho = (T)rho0[k];
+    T u[3] = {0, 0, 0};
+    if (has_u)
+        for (int a = 0; a < L::D; ++a) u[a] = (T)u0[a * cn + k];
+    const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T rref = phys<T>(p).rho_ref;
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const T cu = (T)L::cx(i) * u[0] + (T)L::cy(i) * u[1] + (T)L::cz(i) * u[2];
+        const T feq = (T)L::w(i) * rho * ((T)1 - (T)1.5 * usq + (T)3 * cu + (T)4.5 * cu * cu);
+        Store<S>::st(A + (long long)i * p.pstride + s, Store<S>::SHIFT ? feq - (T)L::w(i) * rref : feq);
+    });
+}
+
+// -------------------------------------------------------------- moments (a6)
+template <class L, class S>
+__global__ void k_moments(KParams p, const S *__restrict__ A, const typename Store<S>::PsiT *__restrict__ psi, int odd,
+                          double *__restrict__ rho_out, double *__restrict__ u_out, double *__restrict__ p_out,
+                          long long c0, long long cn) {
+    using T = typename Store<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cn) return;
+    const long long s = c0 + k;
+    int x, y, z;
+    cell_coords(p, s, x, y, z);
+    const Nbr nb = neighbours(p, x, y, z);
+    T f[L::Q];
+    load_pops<L, S>(p, A, x, y, z, nb, s, odd != 0, f);
+    T rho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        rho += f[i];
+        j[0] += (T)L::cx(i) * f[i];
+        j[1] += (T)L::cy(i) * f[i];
+        j[2] += (T)L::cz(i) * f[i];
+    }
+    T F[3];
+    cell_force<L, T>(p, psi, psi_index(p, x, y, z), F);
+    if (rho_out) rho_out[k] = (double)rho;
+    if (u_out)
+        for (int a = 0; a < L::D; ++a) u_out[a * cn + k] = (double)((j[a] + (T)0.5 * F[a]) / rho);
+    if (p_out) p_out[k] = (double)eos_pressure<T>(p, rho);
+}
+
+// ------------------------------------------------------ population exchange
+template <class L, class S>
+__global__ void k_get_pops(KParams p, const S *__restrict__ A, int odd, double *__restrict__ out, long long c0,
+                           long long cn) {
+    using T = typename Store<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cn) return;
+    const long long s = c0 + k;
+    int x, y, z;
+    cell_coords(p, s, x, y, z);
+    const Nbr nb = neighbours(p, x, y, z);
+    T f[L::Q];
+    load_pops<L, S>(p, A, x, y, z, nb, s, odd != 0, f);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) out[i * cn + k] = (double)f[i];
+}
+
+template <class L, class S>
+__global__ void k_set_pops(KParams p, S *__restrict__ A, const double *__restrict__ in, long long c0, long long cn) {
+    using T = typename Store<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cn) return;
+    const long long s = c0 + k;
+    const T rref = phys<T>(p).rho_ref;
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const T v = (T)in[i * cn + k];
+        Store<S>::st(A + (long long)i * p.pstride + s, Store<S>::SHIFT ? v - (T)L::w(i) * rref : v);
+    });
+}
+
+// ----------------------------------------------------------- reductions (a4)
+// Per-thread FP64 accumulation over a grid-stride loop, warp-shuffle tree, one
+// partial per block (4 doubles); plb_reduce_final sums the partials in block order.
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_reduce(KParams p, const S *__restrict__ A,
+                                                const typename Store<S>::PsiT *__restrict__ psi, int odd, int what,
+                                                int lox, int loy, int loz, int hix, int hiy, int hiz,
+                                                double *__restrict__ partials) {
+    using T = typename Store<S>::T;
+    double acc[4] = {0, 0, 0, 0};
+    const bool is_max = (what == 2);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < p.n; s += stride) {
+        int x, y, z;
+        cell_coords(p, s, x, y, z);
+        if (x < lox || x >= hix || y < loy || y >= hiy || z < loz || z >= hiz) continue;
+        const Nbr nb = neighbours(p, x, y, z);
+        T f[L::Q];
+        load_pops<L, S>(p, A, x, y, z, nb, s, odd != 0, f);
+        double rho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            rho += (double)f[i];
+            j[0] += (double)(L::cx(i) * f[i]);
+            j[1] += (double)(L::cy(i) * f[i]);
+            j[2] += (double)(L::cz(i) * f[i]);
+        }
+        if (what == 0 || what == 5) {
+            acc[0] += rho;
+        } else if (what == 6) {
+            acc[0] += (double)eos_pressure<T>(p, (T)rho);
+        } else {
+            T F[3];
+            cell_force<L, T>(p, psi, psi_index(p, x, y, z), F);
+            const double m[3] = {j[0] + 0.5 * (double)F[0], j[1] + 0.5 * (double)F[1], j[2] + 0.5 * (double)F[2]};
+            if (what == 1) {
+                acc[0] += m[0];
+                acc[1] += m[1];
+                acc[2] += m[2];
+            } else {
+                const double u2 = (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / (rho * rho);
+                if (what == 2) acc[0] = fmax(acc[0], sqrt(u2));
+                else if (what == 3) acc[0] += sqrt(u2);
+                else acc[0] += u2;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = is_max ? fmax(v, w) : v + w;
+        }
+        acc[c] = v;
+    }
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int c = 0; c < 4; ++c) red[warp][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = is_max ? 0.0 : 0.0;
+        const int nw = blockDim.x >> 5;
+        for (int w = 0; w < nw; ++w) v = is_max ? fmax(v, red[w][threadIdx.x]) : v + red[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = v;
+    }
+}
+
+// ----------------------------------------------------------------- launchers
+template <class L, class S> struct Launch {
+    using PsiT = typename Store<S>::PsiT;
+    static unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+    static void init(const KParams &p, void *A, const double *rho0, const double *u0, long long c0, long long cn,
+                     cudaStream_t st) {
+        k_init<L, S><<<blocks(cn, 256), 256, 0, st>>>(p, (S *)A, rho0, u0, c0, cn, u0 != nullptr);
+    }
+    static Planes<S> planes(const KParams &p, const void *A) {
+        Planes<S> pl;
+        for (int i = 0; i < 19; ++i) pl.p[i] = (S *)A + (i < L::Q ? (long long)i * p.pstride : 0);
+        return pl;
+    }
+    static void dims3(const KParams &p, dim3 &grid, dim3 &block) {
+        int bx = p.nx >= 256 ? 256 : (p.nx + 31) / 32 * 32;
+        int by = 256 / bx;
+        if (by > p.ny) by = p.ny;
+        block = dim3(bx, by, 1);
+        grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+    }
+    template <bool ODD> static void psi_t(const KParams &p, const void *A, void *psi, cudaStream_t st) {
+        dim3 grid, block;
+        dims3(p, grid, block);
+        if (p.n < (1LL << 31))
+            k_psi_fast<L, S, ODD, int><<<grid, block, 0, st>>>(p, planes(p, A), (PsiT *)psi);
+        else
+            k_psi_fast<L, S, ODD, long long><<<grid, block, 0, st>>>(p, planes(p, A), (PsiT *)psi);
+    }
+    static void psi(const KParams &p, const void *A, void *psi, int odd, cudaStream_t st) {
+        if (odd) psi_t<true>(p, A, psi, st);
+        else psi_t<false>(p, A, psi, st);
+    }
+    template <int MRT, bool ODD> static void collide_t(const KParams &p, void *A, const void *psi, cudaStream_t st) {
+        dim3 grid, block;
+        dims3(p, grid, block);
+        if (p.n < (1LL << 31))
+            k_collide_fast<L, S, MRT, ODD, int><<<grid, block, 0, st>>>(p, planes(p, A), (const PsiT *)psi);
+        else
+            k_collide_fast<L, S, MRT, ODD, long long><<<grid, block, 0, st>>>(p, planes(p, A), (const PsiT *)psi);
+    }
+    static void collide_bgk(const KParams &p, void *A, const void *psi, int odd, cudaStream_t st) {
+        if (odd) collide_t<0, true>(p, A, psi, st);
+        else collide_t<0, false>(p, A, psi, st);
+    }
+    static void collide_mrt(const KParams &p, void *A, const void *psi, int odd, cudaStream_t st) {
+        if (odd) collide_t<1, true>(p, A, psi, st);
+        else collide_t<1, false>(p, A, psi, st);
+    }
+    static void moments(const KParams &p, const void *A, const void *psi, int odd, double *r, double *u, double *pr,
+                        long long c0, long long cn, cudaStream_t st) {
+        k_moments<L, S><<<blocks(cn, 256), 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, r, u, pr, c0, cn);
+    }
+    static void get_pops(const KParams &p, const void *A, int odd, double *out, long long c0, long long cn,
+                         cudaStream_t st) {
+        k_get_pops<L, S><<<blocks(cn, 256), 256, 0, st>>>(p, (const S *)A, odd, out, c0, cn);
+    }
+    static void set_pops(const KParams &p, void *A, const double *in, long long c0, long long cn, cudaStream_t st) {
+        k_set_pops<L, S><<<blocks(cn, 256), 256, 0, st>>>(p, (S *)A, in, c0, cn);
+    }
+    static void reduce(const KParams &p, const void *A, const void *psi, int odd, int what, const int lo[3],
+                       const int hi[3], double *partials, int nblocks, cudaStream_t st) {
+        k_reduce<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, what, lo[0], lo[1], lo[2],
+                                                hi[0], hi[1], hi[2], partials);
+    }
+    static constexpr Launchers table() {
+        return Launchers{&init, &psi, {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce};
+    }
+};
+
+}  // namespace plb

@@ -1,0 +1,59 @@
+// Host-visible kernel parameter block and launcher table (one table per
+// lattice x storage precision, defined in plb_kern_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace plb {
+
+enum : unsigned { FLAG_PSI_DOMAIN = 1u, FLAG_NONFINITE = 2u };
+
+// Physical parameters in the arithmetic precision of a kernel (FP64 and FP32 copies are
+// both filled on the host, so no kernel converts a double per thread).
+template <class T> struct Phys {
+    T G, A_m1m2, B_m1tr;      // F = -G psi M1 + A (M2 . M1) + B M1 tr(M2) + fext
+    T inv_G;                  // 1 / G
+    T tau_l, tau_v, tau_rho_v, inv_drho_tau;
+    T om_const;               // 1 / tau_l (constant-tau case)
+    T s_rate[6];              // MRT rate by Ghosts::kind (1..5)
+    T fext[3];
+    T rho_ref;                // FP16S shift
+    T pr_RT, pr_b, pr_aalpha;
+    T pe_P, pe_rv, pe_rl, pe_sv;
+    T p_scale;
+};
+
+struct KParams {
+    int nx, ny, nz;
+    long long n;          // cells
+    long long pstride;    // elements between population planes
+    int wall_y;
+    // padded psi array: ghost layer of 1 in y (and z for 3-D), gx in x
+    int px;               // row pitch in elements
+    int py;               // rows per plane (ny + 2)
+    long long psi_origin; // element offset of interior cell (0, 0, 0)
+    int var_tau;
+    int eos_kind;         // 0 PR, 1 paper
+    Phys<double> d;
+    Phys<float> f;
+    unsigned *flags;
+};
+
+struct Launchers {
+    void (*init)(const KParams &, void *A, const double *rho0, const double *u0, long long c0, long long cn,
+                 cudaStream_t);
+    void (*psi)(const KParams &, const void *A, void *psi, int odd, cudaStream_t);
+    void (*collide[2])(const KParams &, void *A, const void *psi, int odd, cudaStream_t);   // [BGK, MRT]
+    void (*moments)(const KParams &, const void *A, const void *psi, int odd, double *rho, double *u, double *p,
+                    long long c0, long long cn, cudaStream_t);
+    void (*get_pops)(const KParams &, const void *A, int odd, double *out, long long c0, long long cn, cudaStream_t);
+    void (*set_pops)(const KParams &, void *A, const double *in, long long c0, long long cn, cudaStream_t);
+    void (*reduce)(const KParams &, const void *A, const void *psi, int odd, int what, const int lo[3],
+                   const int hi[3], double *partials, int nblocks, cudaStream_t);
+};
+
+// Defined in plb_kern_fp64.cu / plb_kern_fp32.cu / plb_kern_fp16.cu; lattice 0 = D2Q9, 1 = D3Q19.
+const Launchers *launchers_fp64(int lattice);
+const Launchers *launchers_fp32(int lattice);
+const Launchers *launchers_fp16(int lattice);
+
+}  // namespace plb

@@ -1,0 +1,542 @@
+// C ABI of the P-LBM library (include/plb.h): handle management, workspace layout,
+// host<->device staging, and the launch sequence of one time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "plb.h"
+#include "plb_host.h"
+#include "plb_launch.h"
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define PLB_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(PLB_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr unsigned MAGIC = 0x504c4231u;   // "PLB1"
+}  // namespace
+
+namespace plb {
+
+bool make_layout(int lattice, const int dims[3], int precision, Layout &L) {
+    if (lattice != PLB_D2Q9 && lattice != PLB_D3Q19) return false;
+    if (precision < PLB_FP64 || precision > PLB_FP16S) return false;
+    if (!dims || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return false;
+    if (lattice == PLB_D2Q9 && dims[2] != 1) return false;
+    L.Q = lattice == PLB_D2Q9 ? 9 : 19;
+    L.D = lattice == PLB_D2Q9 ? 2 : 3;
+    L.n = (long long)dims[0] * dims[1] * dims[2];
+    if (L.n > (1LL << 40)) return false;
+    L.s_pop = precision == PLB_FP64 ? 8 : (precision == PLB_FP32 ? 4 : 2);
+    L.s_psi = precision == PLB_FP64 ? 8 : 4;
+    L.pstride = (L.n + 127) / 128 * 128;
+    L.gx = 16 / L.s_psi;
+    L.px = (int)((dims[0] + 2 * L.gx + 31) / 32 * 32);
+    L.py = dims[1] + 2;
+    L.pz = L.D == 3 ? dims[2] + 2 : 1;
+    L.psi_elems = (long long)L.px * L.py * L.pz;
+    L.chunk = L.n < (1LL << 18) ? L.n : (1LL << 18);
+    L.max_blocks = 1024;
+    size_t off = 0;
+    L.off_pops = off;
+    off = align256(off + (size_t)L.Q * L.pstride * L.s_pop);
+    L.off_psi = off;
+    off = align256(off + (size_t)L.psi_elems * L.s_psi);
+    L.off_partials = off;
+    off = align256(off + (size_t)L.max_blocks * 4 * sizeof(double));
+    L.off_out = off;
+    off = align256(off + 4 * sizeof(double));
+    L.off_staging = off;
+    const int per_cell = L.Q > L.D + 2 ? L.Q : L.D + 2;
+    off = align256(off + (size_t)L.chunk * per_cell * sizeof(double));
+    L.off_flags = off;
+    off = align256(off + 64);
+    L.total = off;
+    return true;
+}
+
+}  // namespace plb
+
+struct plb_state {
+    int lattice;
+    int dims[3];
+    plb_opts opts;
+    plb_eos_params eos;
+    double tau, G, eps;
+    double rho_v, rho_l, p0;   // coexistence densities of the EOS (p_scale = 1)
+    plb::Layout lay;
+    plb::KParams kp;
+    const plb::Launchers *L;
+    char *ws;
+    cudaStream_t stream;
+    long long t;
+    int odd;
+};
+
+namespace {
+
+void reduce_final_launch(const double *partials, int nblocks, int is_max, double *out, cudaStream_t st);
+
+const plb::Launchers *launchers_for(int lattice, int precision) {
+    switch (precision) {
+        case PLB_FP64: return plb::launchers_fp64(lattice);
+        case PLB_FP32: return plb::launchers_fp32(lattice);
+        default: return plb::launchers_fp16(lattice);
+    }
+}
+
+void *pops_ptr(plb_t *h) { return h->ws + h->lay.off_pops; }
+void *psi_ptr(plb_t *h) { return h->ws + h->lay.off_psi; }
+double *staging_ptr(plb_t *h) { return reinterpret_cast<double *>(h->ws + h->lay.off_staging); }
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PLB_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return PLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *plb_last_error(void) { return g_err.c_str(); }
+
+void plb_default_opts(plb_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->kappa = 1.0;
+    o->tau_v = 0.0;
+    o->collision = PLB_BGK;
+    o->s_e = o->s_eps = o->s_q = o->s_pi = o->s_m = 1.0;
+    o->precision = PLB_FP32;
+    o->rho_ref = 0.0;
+    o->wall_y = 0;
+}
+
+int plb_velocity_set(int lattice, int *c, double *w) {
+    static const int c2[9][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+    static const int c3[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                                  {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    if (lattice == PLB_D2Q9) {
+        for (int i = 0; i < 9; ++i) {
+            if (c) {
+                c[3 * i] = c2[i][0];
+                c[3 * i + 1] = c2[i][1];
+                c[3 * i + 2] = 0;
+            }
+            if (w) w[i] = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        }
+        return 9;
+    }
+    if (lattice == PLB_D3Q19) {
+        for (int i = 0; i < 19; ++i) {
+            if (c)
+                for (int a = 0; a < 3; ++a) c[3 * i + a] = c3[i][a];
+            if (w) w[i] = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+        }
+        return 19;
+    }
+    return -1;
+}
+
+size_t plb_workspace_bytes(int lattice, const int dims[3], const plb_opts *opts) {
+    plb_opts o;
+    plb_default_opts(&o);
+    if (opts) o = *opts;
+    plb::Layout L;
+    if (!plb::make_layout(lattice, dims, o.precision, L)) return 0;
+    return L.total;
+}
+
+int plb_solve_params(const plb_eos_params *eos, double *rho_v, double *rho_l, double *p0) {
+    if (!eos) return fail(PLB_EINVAL, "eos is NULL");
+    double rv = 0, rl = 0, pp = 0;
+    int st = plb::solve_coexistence(*eos, rv, rl, pp);
+    if (st != PLB_OK) return fail(st, "no liquid-vapour coexistence for these EOS parameters");
+    if (rho_v) *rho_v = rv;
+    if (rho_l) *rho_l = rl;
+    if (p0) *p0 = pp;
+    return PLB_OK;
+}
+
+int plb_si_convert(const double si[6], const double lat[3], double xi, double out[11]) {
+    if (!si || !lat || !out) return fail(PLB_EINVAL, "NULL argument");
+    int st = plb::si_convert(si, lat, xi, out);
+    if (st != PLB_OK) return fail(st, "invalid physical or lattice inputs");
+    return PLB_OK;
+}
+
+int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
+               const plb_opts *opts, void *dev_workspace, size_t ws_bytes, void *cuda_stream, plb_t **out) {
+    if (!out) return fail(PLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!eos) return fail(PLB_EINVAL, "eos is NULL");
+    plb_opts o;
+    plb_default_opts(&o);
+    if (opts) o = *opts;
+    plb::Layout lay;
+    if (!plb::make_layout(lattice, dims, o.precision, lay)) return fail(PLB_EINVAL, "bad lattice, dims or precision");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(PLB_EINVAL, "tau must be > 1/2");
+    if (!(G < 0.0) || !std::isfinite(G)) return fail(PLB_EINVAL, "G must be negative");
+    if (!std::isfinite(eps) || !std::isfinite(o.kappa)) return fail(PLB_EINVAL, "eps and kappa must be finite");
+    if (o.collision != PLB_BGK && o.collision != PLB_MRT) return fail(PLB_EINVAL, "bad collision");
+    if (o.tau_v > 0.0 && !(o.tau_v > 0.5)) return fail(PLB_EINVAL, "tau_v must be > 1/2");
+    if (eos->kind == PLB_EOS_PR) {
+        if (!(eos->a > 0 && eos->b > 0 && eos->R > 0 && eos->T_over_Tc > 0)) return fail(PLB_EINVAL, "bad PR constants");
+    } else if (eos->kind == PLB_EOS_PAPER) {
+        if (!(eos->rho_v > 0 && eos->rho_l > eos->rho_v && eos->pc_over_rhoc3 > 0))
+            return fail(PLB_EINVAL, "bad paper-EOS constants");
+    } else {
+        return fail(PLB_EINVAL, "unknown EOS kind");
+    }
+    if (!(eos->p_scale >= 0.0)) return fail(PLB_EINVAL, "p_scale must be >= 0");
+    if (!dev_workspace) return fail(PLB_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return fail(PLB_EINVAL, "workspace not 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(PLB_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, lay.total);
+
+    plb_t *h = new plb_state();
+    h->lattice = lattice;
+    std::memcpy(h->dims, dims, sizeof(h->dims));
+    h->opts = o;
+    h->eos = *eos;
+    h->tau = tau;
+    h->G = G;
+    h->eps = eps;
+    h->lay = lay;
+    h->ws = static_cast<char *>(dev_workspace);
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->t = 0;
+    h->odd = 0;
+    h->L = launchers_for(lattice, o.precision);
+    // Coexistence densities: defaults for the tau interpolation and the FP16 shift.
+    double rv = 0, rl = 0, pp = 0;
+    if (plb::solve_coexistence(*eos, rv, rl, pp) != PLB_OK) {
+        rv = rl = pp = 0;
+    }
+    h->rho_v = rv;
+    h->rho_l = rl;
+    h->p0 = pp;
+
+    plb::KParams &k = h->kp;
+    std::memset(&k, 0, sizeof(k));
+    k.nx = dims[0];
+    k.ny = dims[1];
+    k.nz = dims[2];
+    k.n = lay.n;
+    k.pstride = lay.pstride;
+    k.wall_y = o.wall_y ? 1 : 0;
+    k.px = lay.px;
+    k.py = lay.py;
+    k.psi_origin = lay.gx + (long long)lay.px * (1 + (long long)lay.py * (lay.D == 3 ? 1 : 0));
+    plb::Phys<double> &d = k.d;
+    d.G = G;
+    d.inv_G = 1.0 / G;
+    // Eq. interactionForce with the eps coefficient that realises Eq. New_Pressure_Tensor.
+    d.A_m1m2 = -(G / 12.0) * (2.0 * o.kappa - 2.0 - 3.0 * eps);
+    d.B_m1tr = (G / 6.0) * (o.kappa - 1.0);
+    d.tau_l = tau;
+    d.om_const = 1.0 / tau;
+    k.var_tau = o.tau_v > 0.0 && o.tau_v != tau;
+    d.tau_v = k.var_tau ? o.tau_v : tau;
+    double trv = o.tau_rho_v, trl = o.tau_rho_l;
+    if (k.var_tau && !(trl > trv)) {
+        trv = rv;
+        trl = rl;
+        if (!(trl > trv)) {
+            delete h;
+            return fail(PLB_EINVAL, "tau(rho) needs tau_rho_l > tau_rho_v (EOS has no coexistence to default to)");
+        }
+    }
+    d.tau_rho_v = trv;
+    d.inv_drho_tau = k.var_tau ? 1.0 / (trl - trv) : 0.0;
+    d.s_rate[0] = 0.0;
+    d.s_rate[1] = o.s_e;
+    d.s_rate[2] = o.s_eps;
+    d.s_rate[3] = o.s_q;
+    d.s_rate[4] = o.s_pi;
+    d.s_rate[5] = o.s_m;
+    for (int a = 0; a < 3; ++a) d.fext[a] = a < lay.D ? o.body_force[a] : 0.0;
+    d.rho_ref = o.precision == PLB_FP16S ? (o.rho_ref > 0 ? o.rho_ref : rv) : 0.0;
+    h->opts.rho_ref = d.rho_ref;
+    k.eos_kind = eos->kind;
+    if (eos->kind == PLB_EOS_PR) {
+        const plb::PrConstants c = plb::pr_constants(*eos);
+        d.pr_RT = c.RT;
+        d.pr_b = eos->b;
+        d.pr_aalpha = c.aalpha;
+    } else {
+        d.pe_P = eos->pc_over_rhoc3;
+        d.pe_rv = eos->rho_v;
+        d.pe_rl = eos->rho_l;
+        d.pe_sv = std::sqrt(eos->rho_v);
+    }
+    d.p_scale = eos->p_scale;
+    // FP32 copy (rounded once here, not per thread)
+    plb::Phys<float> &f = k.f;
+    const double *src = reinterpret_cast<const double *>(&d);
+    float *dst = reinterpret_cast<float *>(&f);
+    static_assert(sizeof(plb::Phys<double>) == 2 * sizeof(plb::Phys<float>), "Phys layout");
+    for (size_t m = 0; m < sizeof(plb::Phys<double>) / sizeof(double); ++m) dst[m] = (float)src[m];
+    k.flags = reinterpret_cast<unsigned *>(h->ws + lay.off_flags);
+    cudaError_t e = cudaMemsetAsync(h->ws + lay.off_psi, 0, (size_t)lay.psi_elems * lay.s_psi, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(k.flags, 0, 64, h->stream);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(PLB_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PLB_OK;
+}
+
+void plb_destroy(plb_t *h) { delete h; }
+
+long long plb_time(const plb_t *h) { return h ? h->t : -1; }
+
+int plb_init(plb_t *h, const double *rho0, const double *u0) {
+    if (!h || !rho0) return fail(PLB_EINVAL, "NULL argument");
+    const long long n = h->lay.n;
+    for (long long s = 0; s < n; ++s)
+        if (!(rho0[s] > 0.0) || !std::isfinite(rho0[s])) return fail(PLB_EINVAL, "rho0[%lld] is not a positive number", s);
+    if (u0)
+        for (long long s = 0; s < (long long)h->lay.D * n; ++s)
+            if (!std::isfinite(u0[s])) return fail(PLB_EINVAL, "u0[%lld] is not finite", s);
+    double *stg = staging_ptr(h);
+    const long long chunk = h->lay.chunk;
+    for (long long c0 = 0; c0 < n; c0 += chunk) {
+        const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
+        PLB_CUDA(cudaMemcpyAsync(stg, rho0 + c0, cn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        if (u0)
+            for (int a = 0; a < h->lay.D; ++a)
+                PLB_CUDA(cudaMemcpyAsync(stg + (1 + a) * cn, u0 + a * n + c0, cn * sizeof(double),
+                                         cudaMemcpyHostToDevice, h->stream));
+        h->L->init(h->kp, pops_ptr(h), stg, u0 ? stg + cn : nullptr, c0, cn, h->stream);
+        int st = check_launch();
+        if (st) return st;
+    }
+    PLB_CUDA(cudaMemsetAsync(h->kp.flags, 0, 64, h->stream));
+    h->t = 0;
+    h->odd = 0;
+    return PLB_OK;
+}
+
+int plb_step(plb_t *h, int n) {
+    if (!h || n < 0) return fail(PLB_EINVAL, "bad argument");
+    const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
+    for (int k = 0; k < n; ++k) {
+        h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+        h->L->collide[coll](h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+        h->odd ^= 1;
+        h->t += 1;
+    }
+    return check_launch();
+}
+
+int plb_step_timed(plb_t *h, int n, double ms[2]) {
+    if (!h || n < 0 || !ms) return fail(PLB_EINVAL, "bad argument");
+    ms[0] = ms[1] = 0.0;
+    if (n == 0) return PLB_OK;
+    const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
+    std::vector<cudaEvent_t> ev(2 * (size_t)n + 1);
+    for (auto &e : ev) PLB_CUDA(cudaEventCreate(&e));
+    int st = PLB_OK;
+    PLB_CUDA(cudaEventRecord(ev[0], h->stream));
+    for (int k = 0; k < n; ++k) {
+        h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+        cudaEventRecord(ev[2 * k + 1], h->stream);
+        h->L->collide[coll](h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+        cudaEventRecord(ev[2 * k + 2], h->stream);
+        h->odd ^= 1;
+        h->t += 1;
+    }
+    st = check_launch();
+    cudaError_t e = cudaEventSynchronize(ev[2 * n]);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+        cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
+        ms[0] += a;
+        ms[1] += b;
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(PLB_ECUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+    return st;
+}
+
+int plb_status(plb_t *h) {
+    if (!h) return fail(PLB_EINVAL, "NULL handle");
+    unsigned flags = 0;
+    PLB_CUDA(cudaMemcpyAsync(&flags, h->kp.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    if (flags & plb::FLAG_NONFINITE) return fail(PLB_ENONFINITE, "a density became non-positive or non-finite");
+    if (flags & plb::FLAG_PSI_DOMAIN) return fail(PLB_EPSI_DOMAIN, "2 (p_EOS - rho/3) / G < 0 on some cell");
+    return PLB_OK;
+}
+
+int plb_moments(plb_t *h, double *rho, double *u, double *p) {
+    if (!h) return fail(PLB_EINVAL, "NULL handle");
+    h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+    const long long n = h->lay.n, chunk = h->lay.chunk;
+    const int D = h->lay.D;
+    double *stg = staging_ptr(h);
+    for (long long c0 = 0; c0 < n; c0 += chunk) {
+        const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
+        double *srho = stg, *su = stg + cn, *sp = stg + (1 + D) * cn;
+        h->L->moments(h->kp, pops_ptr(h), psi_ptr(h), h->odd, rho ? srho : nullptr, u ? su : nullptr,
+                      p ? sp : nullptr, c0, cn, h->stream);
+        int st = check_launch();
+        if (st) return st;
+        if (rho) PLB_CUDA(cudaMemcpyAsync(rho + c0, srho, cn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (u)
+            for (int a = 0; a < D; ++a)
+                PLB_CUDA(cudaMemcpyAsync(u + a * n + c0, su + a * cn, cn * sizeof(double), cudaMemcpyDeviceToHost,
+                                         h->stream));
+        if (p) PLB_CUDA(cudaMemcpyAsync(p + c0, sp, cn * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    return plb_status(h);
+}
+
+int plb_reduce(plb_t *h, int what, const int lo[3], const int hi[3], double *out) {
+    if (!h || !out) return fail(PLB_EINVAL, "NULL argument");
+    if (what < PLB_MASS || what > PLB_MEAN_P) return fail(PLB_EINVAL, "unknown reduction %d", what);
+    int blo[3] = {0, 0, 0}, bhi[3] = {h->dims[0], h->dims[1], h->dims[2]};
+    if (lo)
+        for (int a = 0; a < 3; ++a) blo[a] = lo[a] < 0 ? 0 : lo[a];
+    if (hi)
+        for (int a = 0; a < 3; ++a) bhi[a] = hi[a] > h->dims[a] ? h->dims[a] : hi[a];
+    long long count = 1;
+    for (int a = 0; a < 3; ++a) count *= (bhi[a] > blo[a] ? bhi[a] - blo[a] : 0);
+    if (count == 0) return fail(PLB_EINVAL, "empty box");
+    const bool needs_force = what == PLB_MOMENTUM || what == PLB_UMAX || what == PLB_UL1 || what == PLB_UL2;
+    if (needs_force) h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
+    long long nb = (h->lay.n + 255) / 256;
+    const int nblocks = (int)(nb < h->lay.max_blocks ? nb : h->lay.max_blocks);
+    double *partials = reinterpret_cast<double *>(h->ws + h->lay.off_partials);
+    double *dout = reinterpret_cast<double *>(h->ws + h->lay.off_out);
+    h->L->reduce(h->kp, pops_ptr(h), psi_ptr(h), h->odd, what, blo, bhi, partials, nblocks, h->stream);
+    int st = check_launch();
+    if (st) return st;
+    reduce_final_launch(partials, nblocks, what == PLB_UMAX, dout, h->stream);
+    st = check_launch();
+    if (st) return st;
+    double res[4];
+    PLB_CUDA(cudaMemcpyAsync(res, dout, sizeof(res), cudaMemcpyDeviceToHost, h->stream));
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    switch (what) {
+        case PLB_MOMENTUM: out[0] = res[0]; out[1] = res[1]; out[2] = res[2]; break;
+        case PLB_UL2: out[0] = std::sqrt(res[0]); break;
+        case PLB_MEAN_RHO:
+        case PLB_MEAN_P: out[0] = res[0] / (double)count; break;
+        default: out[0] = res[0];
+    }
+    return plb_status(h);
+}
+
+int plb_get_populations(plb_t *h, double *f) {
+    if (!h || !f) return fail(PLB_EINVAL, "NULL argument");
+    const long long n = h->lay.n, chunk = h->lay.chunk;
+    double *stg = staging_ptr(h);
+    for (long long c0 = 0; c0 < n; c0 += chunk) {
+        const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
+        h->L->get_pops(h->kp, pops_ptr(h), h->odd, stg, c0, cn, h->stream);
+        int st = check_launch();
+        if (st) return st;
+        for (int i = 0; i < h->lay.Q; ++i)
+            PLB_CUDA(cudaMemcpyAsync(f + i * n + c0, stg + i * cn, cn * sizeof(double), cudaMemcpyDeviceToHost,
+                                     h->stream));
+    }
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    return PLB_OK;
+}
+
+int plb_set_populations(plb_t *h, const double *f) {
+    if (!h || !f) return fail(PLB_EINVAL, "NULL argument");
+    const long long n = h->lay.n, chunk = h->lay.chunk;
+    double *stg = staging_ptr(h);
+    for (long long c0 = 0; c0 < n; c0 += chunk) {
+        const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
+        for (int i = 0; i < h->lay.Q; ++i)
+            PLB_CUDA(cudaMemcpyAsync(stg + i * cn, f + i * n + c0, cn * sizeof(double), cudaMemcpyHostToDevice,
+                                     h->stream));
+        h->L->set_pops(h->kp, pops_ptr(h), stg, c0, cn, h->stream);
+        int st = check_launch();
+        if (st) return st;
+    }
+    h->odd = 0;
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    return PLB_OK;
+}
+
+size_t plb_state_bytes(const plb_t *h) {
+    if (!h) return 0;
+    return 64 + (size_t)h->lay.Q * h->lay.pstride * h->lay.s_pop;
+}
+
+int plb_get_state(plb_t *h, void *host_buf, size_t bytes) {
+    if (!h || !host_buf) return fail(PLB_EINVAL, "NULL argument");
+    if (bytes < plb_state_bytes(h)) return fail(PLB_ENOMEM, "state buffer too small");
+    long long hdr[8] = {(long long)MAGIC, h->lattice, h->opts.precision, h->dims[0], h->dims[1], h->dims[2], h->t,
+                        h->odd};
+    std::memcpy(host_buf, hdr, sizeof(hdr));
+    PLB_CUDA(cudaMemcpyAsync(static_cast<char *>(host_buf) + 64, pops_ptr(h), plb_state_bytes(h) - 64,
+                             cudaMemcpyDeviceToHost, h->stream));
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    return PLB_OK;
+}
+
+int plb_set_state(plb_t *h, const void *host_buf, size_t bytes) {
+    if (!h || !host_buf) return fail(PLB_EINVAL, "NULL argument");
+    if (bytes < plb_state_bytes(h)) return fail(PLB_ENOMEM, "state buffer too small");
+    long long hdr[8];
+    std::memcpy(hdr, host_buf, sizeof(hdr));
+    if (hdr[0] != (long long)MAGIC || hdr[1] != h->lattice || hdr[2] != h->opts.precision || hdr[3] != h->dims[0] ||
+        hdr[4] != h->dims[1] || hdr[5] != h->dims[2])
+        return fail(PLB_EINVAL, "state does not match this lattice");
+    PLB_CUDA(cudaMemcpyAsync(pops_ptr(h), static_cast<const char *>(host_buf) + 64, plb_state_bytes(h) - 64,
+                             cudaMemcpyHostToDevice, h->stream));
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
+    h->t = hdr[6];
+    h->odd = (int)hdr[7];
+    return PLB_OK;
+}
+
+}  // extern "C"
+
+// Final pass of the reductions: one warp sums the block partials in a fixed order.
+namespace {
+__global__ void k_reduce_final(const double *__restrict__ partials, int nblocks, int is_max, double *__restrict__ out) {
+    const int c = threadIdx.x;
+    if (c >= 4) return;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v = is_max ? fmax(v, partials[b * 4 + c]) : v + partials[b * 4 + c];
+    out[c] = v;
+}
+
+void reduce_final_launch(const double *partials, int nblocks, int is_max, double *out, cudaStream_t st) {
+    k_reduce_final<<<1, 32, 0, st>>>(partials, nblocks, is_max, out);
+}
+}  // namespace
