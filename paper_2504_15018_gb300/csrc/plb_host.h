@@ -30,4 +30,17 @@ struct Layout {
 
 bool make_layout(int lattice, const int dims[3], int precision, Layout &L);
 
+struct KParams;
+struct Launchers;
+
+// Records the message of a failure for plb_last_error() and returns code.
+int set_error(int code, const char *fmt, ...);
+// Validation shared by the lattice constructors; o receives the options in effect.
+int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
+                      const plb_opts *opts, plb_opts &o, Layout &lay);
+// Kernel parameter block of a lattice (everything but the device pointers).
+int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, double G, double eps, const plb_opts &o,
+                 const Layout &lay, double rho_v, double rho_l, KParams &k);
+const Launchers *launchers_for_precision(int lattice, int precision);
+
 }  // namespace plb

@@ -16,8 +16,10 @@
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
 
-int fail(int code, const char *fmt, ...) {
+namespace plb {
+int set_error(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -26,6 +28,10 @@ int fail(int code, const char *fmt, ...) {
     g_err = buf;
     return code;
 }
+}  // namespace plb
+
+namespace {
+#define fail plb::set_error
 
 #define PLB_CUDA(call)                                                                       \
     do {                                                                                     \
@@ -189,16 +195,16 @@ int plb_si_convert(const double si[6], const double lat[3], double xi, double ou
     return PLB_OK;
 }
 
-int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
-               const plb_opts *opts, void *dev_workspace, size_t ws_bytes, void *cuda_stream, plb_t **out) {
-    if (!out) return fail(PLB_EINVAL, "out is NULL");
-    *out = nullptr;
+}  // extern "C"
+
+namespace plb {
+
+int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
+                      const plb_opts *opts, plb_opts &o, Layout &lay) {
     if (!eos) return fail(PLB_EINVAL, "eos is NULL");
-    plb_opts o;
     plb_default_opts(&o);
     if (opts) o = *opts;
-    plb::Layout lay;
-    if (!plb::make_layout(lattice, dims, o.precision, lay)) return fail(PLB_EINVAL, "bad lattice, dims or precision");
+    if (!make_layout(lattice, dims, o.precision, lay)) return fail(PLB_EINVAL, "bad lattice, dims or precision");
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(PLB_EINVAL, "tau must be > 1/2");
     if (!(G < 0.0) || !std::isfinite(G)) return fail(PLB_EINVAL, "G must be negative");
     if (!std::isfinite(eps) || !std::isfinite(o.kappa)) return fail(PLB_EINVAL, "eps and kappa must be finite");
@@ -213,6 +219,84 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
         return fail(PLB_EINVAL, "unknown EOS kind");
     }
     if (!(eos->p_scale >= 0.0)) return fail(PLB_EINVAL, "p_scale must be >= 0");
+    return PLB_OK;
+}
+
+int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, double G, double eps, const plb_opts &o,
+                 const Layout &lay, double rv, double rl, KParams &k) {
+    std::memset(&k, 0, sizeof(k));
+    k.nx = dims[0];
+    k.ny = dims[1];
+    k.nz = dims[2];
+    k.n = lay.n;
+    k.pstride = lay.pstride;
+    k.wall_y = o.wall_y ? 1 : 0;
+    k.px = lay.px;
+    k.py = lay.py;
+    k.psi_origin = lay.gx + (long long)lay.px * (1 + (long long)lay.py * (lay.D == 3 ? 1 : 0));
+    Phys<double> &d = k.d;
+    d.G = G;
+    d.inv_G = 1.0 / G;
+    // Eq. interactionForce with the eps coefficient that realises Eq. New_Pressure_Tensor.
+    d.A_m1m2 = -(G / 12.0) * (2.0 * o.kappa - 2.0 - 3.0 * eps);
+    d.B_m1tr = (G / 6.0) * (o.kappa - 1.0);
+    d.tau_l = tau;
+    d.om_const = 1.0 / tau;
+    k.var_tau = o.tau_v > 0.0 && o.tau_v != tau;
+    d.tau_v = k.var_tau ? o.tau_v : tau;
+    double trv = o.tau_rho_v, trl = o.tau_rho_l;
+    if (k.var_tau && !(trl > trv)) {
+        trv = rv;
+        trl = rl;
+        if (!(trl > trv))
+            return fail(PLB_EINVAL, "tau(rho) needs tau_rho_l > tau_rho_v (EOS has no coexistence to default to)");
+    }
+    d.tau_rho_v = trv;
+    d.inv_drho_tau = k.var_tau ? 1.0 / (trl - trv) : 0.0;
+    d.s_rate[0] = 0.0;
+    d.s_rate[1] = o.s_e;
+    d.s_rate[2] = o.s_eps;
+    d.s_rate[3] = o.s_q;
+    d.s_rate[4] = o.s_pi;
+    d.s_rate[5] = o.s_m;
+    for (int a = 0; a < 3; ++a) d.fext[a] = a < lay.D ? o.body_force[a] : 0.0;
+    d.rho_ref = o.precision == PLB_FP16S ? (o.rho_ref > 0 ? o.rho_ref : rv) : 0.0;
+    k.eos_kind = eos.kind;
+    if (eos.kind == PLB_EOS_PR) {
+        const PrConstants c = pr_constants(eos);
+        d.pr_RT = c.RT;
+        d.pr_b = eos.b;
+        d.pr_aalpha = c.aalpha;
+    } else {
+        d.pe_P = eos.pc_over_rhoc3;
+        d.pe_rv = eos.rho_v;
+        d.pe_rl = eos.rho_l;
+        d.pe_sv = std::sqrt(eos.rho_v);
+    }
+    d.p_scale = eos.p_scale;
+    // FP32 copy (rounded once here, not per thread)
+    Phys<float> &f = k.f;
+    const double *src = reinterpret_cast<const double *>(&d);
+    float *dst = reinterpret_cast<float *>(&f);
+    static_assert(sizeof(Phys<double>) == 2 * sizeof(Phys<float>), "Phys layout");
+    for (size_t m = 0; m < sizeof(Phys<double>) / sizeof(double); ++m) dst[m] = (float)src[m];
+    return PLB_OK;
+}
+
+const Launchers *launchers_for_precision(int lattice, int precision) { return launchers_for(lattice, precision); }
+
+}  // namespace plb
+
+extern "C" {
+
+int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G, double eps,
+               const plb_opts *opts, void *dev_workspace, size_t ws_bytes, void *cuda_stream, plb_t **out) {
+    if (!out) return fail(PLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    plb_opts o;
+    plb::Layout lay;
+    int st = plb::check_create_args(lattice, dims, eos, tau, G, eps, opts, o, lay);
+    if (st != PLB_OK) return st;
     if (!dev_workspace) return fail(PLB_EINVAL, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return fail(PLB_EINVAL, "workspace not 256-byte aligned");
     if (ws_bytes < lay.total)
@@ -240,67 +324,13 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     h->rho_v = rv;
     h->rho_l = rl;
     h->p0 = pp;
-
     plb::KParams &k = h->kp;
-    std::memset(&k, 0, sizeof(k));
-    k.nx = dims[0];
-    k.ny = dims[1];
-    k.nz = dims[2];
-    k.n = lay.n;
-    k.pstride = lay.pstride;
-    k.wall_y = o.wall_y ? 1 : 0;
-    k.px = lay.px;
-    k.py = lay.py;
-    k.psi_origin = lay.gx + (long long)lay.px * (1 + (long long)lay.py * (lay.D == 3 ? 1 : 0));
-    plb::Phys<double> &d = k.d;
-    d.G = G;
-    d.inv_G = 1.0 / G;
-    // Eq. interactionForce with the eps coefficient that realises Eq. New_Pressure_Tensor.
-    d.A_m1m2 = -(G / 12.0) * (2.0 * o.kappa - 2.0 - 3.0 * eps);
-    d.B_m1tr = (G / 6.0) * (o.kappa - 1.0);
-    d.tau_l = tau;
-    d.om_const = 1.0 / tau;
-    k.var_tau = o.tau_v > 0.0 && o.tau_v != tau;
-    d.tau_v = k.var_tau ? o.tau_v : tau;
-    double trv = o.tau_rho_v, trl = o.tau_rho_l;
-    if (k.var_tau && !(trl > trv)) {
-        trv = rv;
-        trl = rl;
-        if (!(trl > trv)) {
-            delete h;
-            return fail(PLB_EINVAL, "tau(rho) needs tau_rho_l > tau_rho_v (EOS has no coexistence to default to)");
-        }
+    st = plb::fill_kparams(dims, *eos, tau, G, eps, o, lay, rv, rl, k);
+    if (st != PLB_OK) {
+        delete h;
+        return st;
     }
-    d.tau_rho_v = trv;
-    d.inv_drho_tau = k.var_tau ? 1.0 / (trl - trv) : 0.0;
-    d.s_rate[0] = 0.0;
-    d.s_rate[1] = o.s_e;
-    d.s_rate[2] = o.s_eps;
-    d.s_rate[3] = o.s_q;
-    d.s_rate[4] = o.s_pi;
-    d.s_rate[5] = o.s_m;
-    for (int a = 0; a < 3; ++a) d.fext[a] = a < lay.D ? o.body_force[a] : 0.0;
-    d.rho_ref = o.precision == PLB_FP16S ? (o.rho_ref > 0 ? o.rho_ref : rv) : 0.0;
-    h->opts.rho_ref = d.rho_ref;
-    k.eos_kind = eos->kind;
-    if (eos->kind == PLB_EOS_PR) {
-        const plb::PrConstants c = plb::pr_constants(*eos);
-        d.pr_RT = c.RT;
-        d.pr_b = eos->b;
-        d.pr_aalpha = c.aalpha;
-    } else {
-        d.pe_P = eos->pc_over_rhoc3;
-        d.pe_rv = eos->rho_v;
-        d.pe_rl = eos->rho_l;
-        d.pe_sv = std::sqrt(eos->rho_v);
-    }
-    d.p_scale = eos->p_scale;
-    // FP32 copy (rounded once here, not per thread)
-    plb::Phys<float> &f = k.f;
-    const double *src = reinterpret_cast<const double *>(&d);
-    float *dst = reinterpret_cast<float *>(&f);
-    static_assert(sizeof(plb::Phys<double>) == 2 * sizeof(plb::Phys<float>), "Phys layout");
-    for (size_t m = 0; m < sizeof(plb::Phys<double>) / sizeof(double); ++m) dst[m] = (float)src[m];
+    h->opts.rho_ref = k.d.rho_ref;
     k.flags = reinterpret_cast<unsigned *>(h->ws + lay.off_flags);
     cudaError_t e = cudaMemsetAsync(h->ws + lay.off_psi, 0, (size_t)lay.psi_elems * lay.s_psi, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.flags, 0, 64, h->stream);
