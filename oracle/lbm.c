@@ -456,17 +456,19 @@ static void collide_cell(const orc_params *P, const double *fc, const double *F,
         for (int i = 0; i < q; ++i) fpost[i] = fc[i] - (fc[i] - feq[i]) / tau + Fi[i];
         return;
     }
-    double Ft[19], dm[19], mF[19];
+    double Ft[19], fneq[19], dm[19], mF[19];
     guo_bracket(P->lattice, F, u, Ft);
+    for (int i = 0; i < q; ++i) fneq[i] = fc[i] - feq[i];
     for (int k = 0; k < q; ++k) {
-        double m = 0.0, meq = 0.0, mf = 0.0;
+        /* m - m^eq = M (f - f^eq): the same quantity by linearity of M, without
+           subtracting two large moments that nearly cancel */
+        double mneq = 0.0, mf = 0.0;
         for (int i = 0; i < q; ++i) {
-            m += M[k * q + i] * fc[i];
-            meq += M[k * q + i] * feq[i];
+            mneq += M[k * q + i] * fneq[i];
             mf += M[k * q + i] * Ft[i];
         }
         double s = mrt_rate(P, k, tau);
-        dm[k] = s * (m - meq);
+        dm[k] = s * mneq;
         mF[k] = (1.0 - s / 2.0) * mf;
     }
     for (int i = 0; i < q; ++i) {
