@@ -186,6 +186,35 @@ int plb_solve_params(const plb_eos_params *eos, double *rho_v, double *rho_l, do
  * out = {C_L, C_T, C_M, C_U, C_VF, C_gamma, rho_v, tau_v, gamma_lat, pc_over_rhoc3, kappa}. */
 int plb_si_convert(const double si[6], const double lat[3], double xi, double out[11]);
 
+/* Allocation-free stepping, for callers that cannot allocate device memory: a plugin
+ * that lives inside another framework's memory arena and only receives the buffers it
+ * works on, or a real-time loop in which cudaMalloc (which may synchronise the device) is
+ * not allowed.  The paper has no counterpart to this entry point; it is part of this
+ * library's interface only.
+ *
+ * Advances the populations in dev_pops by 2 * npairs time steps with the same kernels as
+ * plb_step.  dev_pops: caller-owned device array of Q * N stored populations, direction-major
+ * f[i * N + s] in the plb_velocity_set() order, element type double (PLB_FP64), float
+ * (PLB_FP32) or half holding f_i - w_i rho_ref (PLB_FP16S); 256-byte aligned; updated in place
+ * and, after an even number of steps, again in this natural layout.  The other arguments are
+ * those of plb_create.
+ *
+ * Scratch: the padded psi field and the error flags live in one file-scope device array of
+ * 8 MiB that every GPU loading this library holds until the process exits.  The padded psi
+ * field must fit in 8 MiB - 256 bytes (padded extents (nx + 2g rounded up to 32) x (ny + 2)
+ * [x (nz + 2)], 4 bytes per value, 8 for PLB_FP64; e.g. a 120^3 D3Q19 lattice in FP32); larger
+ * lattices are rejected with PLB_ENOMEM and a message.  The function calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call shares the array and leaves its contents behind; the flags are
+ * cleared at the start of each call.  Calls whose work overlaps on the GPU (different
+ * streams, or without an ordering between them) race on the array.
+ *
+ * Returns after the steps have finished (synchronises the stream), with PLB_EPSI_DOMAIN or
+ * PLB_ENONFINITE if a kernel met such a cell, PLB_EINVAL / PLB_ENOMEM on bad arguments. */
+int plb_step_pairs_static(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G,
+                          double eps, const plb_opts *opts, void *dev_pops, int npairs, void *cuda_stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char *plb_last_error(void);
 

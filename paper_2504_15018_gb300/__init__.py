@@ -85,6 +85,9 @@ _SIGNATURES = {
     "plb_set_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "plb_solve_params": (ctypes.c_int, [ctypes.POINTER(plb_eos_params), _DP, _DP, _DP]),
     "plb_si_convert": (ctypes.c_int, [_DP, _DP, ctypes.c_double, _DP]),
+    "plb_step_pairs_static": (ctypes.c_int, [ctypes.c_int, _IP, ctypes.POINTER(plb_eos_params), ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.POINTER(plb_opts), _VP,
+                                             ctypes.c_int, _VP]),
     "plb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -234,6 +237,14 @@ def plb_si_convert(si, lat, xi: float) -> dict:
     _check(lib().plb_si_convert((ctypes.c_double * 6)(*si), (ctypes.c_double * 3)(*lat), float(xi), out))
     keys = ["C_L", "C_T", "C_M", "C_U", "C_VF", "C_gamma", "rho_v", "tau_v", "gamma_lat", "P", "kappa"]
     return dict(zip(keys, out[:]))
+
+
+def plb_step_pairs_static(lattice: int, dims, eos: plb_eos_params, tau: float, G: float, eps: float,
+                          opts: plb_opts | None, dev_pops: int, npairs: int, cuda_stream: int):
+    """Allocation-free stepping of a caller-owned device population array (2 * npairs steps)."""
+    _check(lib().plb_step_pairs_static(lattice, _iptr(dims), ctypes.byref(eos), tau, G, eps,
+                                       ctypes.byref(opts) if opts is not None else None, _VP(dev_pops),
+                                       int(npairs), _VP(cuda_stream)))
 
 
 # ------------------------------------------------------------------- helpers

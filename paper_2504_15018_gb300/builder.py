@@ -27,6 +27,7 @@ UNITS = [
     ("plb_kern_fp32.cu", []),
     ("plb_kern_fp16.cu", []),
     ("plb_params.cpp", []),
+    ("plb_noalloc.cu", []),
 ]
 
 
