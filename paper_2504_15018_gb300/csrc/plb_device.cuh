@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+#include "plb_f2.cuh"
 #include "plb_launch.h"
 
 namespace plb {
@@ -296,11 +297,11 @@ __device__ __forceinline__ void cell_force(const KParams &p, const PsiT *__restr
 
 // 1 / tau(rho) of Sec. VI (interpolation weight clamped to [0, 1]).
 template <class T> __device__ __forceinline__ T omega_of(const KParams &p, T rho) {
-    const Phys<T> &q = phys<T>(p);
-    if (!p.var_tau) return q.om_const;
-    T wgt = (rho - q.tau_rho_v) * q.inv_drho_tau;
-    wgt = wgt < (T)0 ? (T)0 : (wgt > (T)1 ? (T)1 : wgt);
-    return fdiv((T)1, mad(wgt, q.tau_l - q.tau_v, q.tau_v));
+    using R = typename ScalarOf<T>::type;
+    const Phys<R> &q = phys<R>(p);
+    if (!p.var_tau) return T(q.om_const);
+    const T wgt = clamp01((rho - T(q.tau_rho_v)) * T(q.inv_drho_tau));
+    return fdiv(T(1), mad(wgt, T(q.tau_l - q.tau_v), T(q.tau_v)));
 }
 
 // Padded psi index of interior cell (x, y, z).

@@ -6,6 +6,7 @@
 
 #include "plb_device.cuh"
 #include "plb_launch.h"
+#include "plb_pair.cuh"
 #include "plb_step.cuh"
 
 namespace plb {
@@ -195,8 +196,28 @@ template <class L, class S> struct Launch {
         block = dim3(bx, by, 1);
         grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
     }
+    // Two cells per thread with packed FP32 arithmetic where it applies (FP32 arithmetic,
+    // even nx, fewer than 2^31 cells); one cell per thread otherwise.
+    static bool use_pair(const KParams &p) {
+        return !std::is_same<S, double>::value && (p.nx % 2 == 0) && p.n < (1LL << 31);
+    }
+    static void dims_pair(const KParams &p, dim3 &grid, dim3 &block) {
+        const int npx = p.nx / 2;
+        int bx = npx >= 256 ? 256 : (npx + 31) / 32 * 32;
+        int by = 256 / bx;
+        if (by > p.ny) by = p.ny;
+        block = dim3(bx, by, 1);
+        grid = dim3((npx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+    }
     template <bool ODD> static void psi_t(const KParams &p, const void *A, void *psi, cudaStream_t st) {
         dim3 grid, block;
+        if constexpr (!std::is_same<S, double>::value) {
+            if (use_pair(p)) {
+                dims_pair(p, grid, block);
+                k_psi_pair<L, S, ODD><<<grid, block, 0, st>>>(p, planes(p, A), (float *)psi);
+                return;
+            }
+        }
         dims3(p, grid, block);
         if (p.n < (1LL << 31))
             k_psi_fast<L, S, ODD, int><<<grid, block, 0, st>>>(p, planes(p, A), (PsiT *)psi);
@@ -209,6 +230,13 @@ template <class L, class S> struct Launch {
     }
     template <int MRT, bool ODD> static void collide_t(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         dim3 grid, block;
+        if constexpr (!std::is_same<S, double>::value) {
+            if (use_pair(p)) {
+                dims_pair(p, grid, block);
+                k_collide_pair<L, S, MRT, ODD><<<grid, block, 0, st>>>(p, planes(p, A), (const float *)psi);
+                return;
+            }
+        }
         dims3(p, grid, block);
         if (p.n < (1LL << 31))
             k_collide_fast<L, S, MRT, ODD, int><<<grid, block, 0, st>>>(p, planes(p, A), (const PsiT *)psi);

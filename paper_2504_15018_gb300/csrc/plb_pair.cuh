@@ -1,0 +1,286 @@
+// Two-cell variants of the step kernels for FP32 arithmetic (FP32 and FP16-shifted storage).
+//
+// Each thread updates the x-adjacent cells (x0, x0 + 1), x0 even, with packed FP32
+// arithmetic (plb_f2.cuh).  nx must be even.  Population I/O per direction:
+//  - aligned pairs (every even-parity access; odd-parity accesses with c_x = 0, whose
+//    row offsets are multiples of nx) move as one 8-byte (FP32) or 4-byte (FP16) access;
+//  - odd-parity accesses with c_x != 0 are shifted by one element and move as two
+//    scalar accesses (per-cell x offsets carry the periodic wrap).
+// The psi stencil of the two cells is read as float2 vectors: 3 per row where the
+// stencil spans x0 - 1 .. x0 + 2, 1 where it spans x0 .. x0 + 1.
+#pragma once
+#include "plb_step.cuh"
+
+namespace plb {
+
+template <class S> struct PairIO;
+template <> struct PairIO<float> {
+    __device__ static f2 ld2(const float *a) { return f2(__ldcs(reinterpret_cast<const float2 *>(a))); }
+    __device__ static f2 ld11(const float *a0, const float *a1) { return f2(__ldcs(a0), __ldcs(a1)); }
+    __device__ static void st2(float *a, f2 v) { __stcs(reinterpret_cast<float2 *>(a), v.v); }
+    __device__ static void st11(float *a0, float *a1, f2 v) {
+        __stcs(a0, v.v.x);
+        __stcs(a1, v.v.y);
+    }
+};
+template <> struct PairIO<__half> {
+    __device__ static f2 ld2(const __half *a) {
+        const unsigned int b = __ldcs(reinterpret_cast<const unsigned int *>(a));
+        __half2 h;
+        *reinterpret_cast<unsigned int *>(&h) = b;
+        return f2(__half22float2(h));
+    }
+    __device__ static f2 ld11(const __half *a0, const __half *a1) {
+        return f2(Store<__half>::ld(a0), Store<__half>::ld(a1));
+    }
+    __device__ static void st2(__half *a, f2 v) {
+        const __half2 h = __floats2half2_rn(v.v.x, v.v.y);
+        __stcs(reinterpret_cast<unsigned int *>(a), *reinterpret_cast<const unsigned int *>(&h));
+    }
+    __device__ static void st11(__half *a0, __half *a1, f2 v) {
+        Store<__half>::st(a0, v.v.x);
+        Store<__half>::st(a1, v.v.y);
+    }
+};
+
+// Geometry of the cell pair: shared row offsets, per-cell x offsets with the wrap.
+struct GeoPair {
+    int x0, y, z;
+    int s0;                      // cell index of x0 (lattices below 2^31 cells)
+    int ox0[3], ox1[3], oy[3], oz[3];
+};
+
+__device__ __forceinline__ bool make_geo_pair(const KParams &p, GeoPair &g) {
+    g.x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    g.y = blockIdx.y * blockDim.y + threadIdx.y;
+    g.z = blockIdx.z;
+    if (g.x0 >= p.nx || g.y >= p.ny) return false;
+    const int row = p.nx, plane = p.nx * p.ny;
+    g.s0 = g.x0 + row * (g.y + p.ny * g.z);
+    g.ox0[0] = g.x0 > 0 ? -1 : p.nx - 1;
+    g.ox0[1] = 0;
+    g.ox0[2] = 1;
+    g.ox1[0] = -1;
+    g.ox1[1] = 0;
+    g.ox1[2] = g.x0 + 1 < p.nx - 1 ? 1 : 1 - p.nx;
+    g.oy[0] = g.y > 0 ? -row : row * (p.ny - 1);
+    g.oy[1] = 0;
+    g.oy[2] = g.y < p.ny - 1 ? row : -row * (p.ny - 1);
+    g.oz[0] = g.z > 0 ? -plane : plane * (p.nz - 1);
+    g.oz[1] = 0;
+    g.oz[2] = g.z < p.nz - 1 ? plane : -plane * (p.nz - 1);
+    return true;
+}
+
+template <class L, class S, bool ODD, bool WALL>
+__device__ __forceinline__ void load_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 *f) {
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int o = opp(i);
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        if (!ODD) {
+            f[i] = PairIO<S>::ld2(A.p[i] + g.s0);
+        } else {
+            bool from_wall = false;
+            if (WALL && cy != 0) from_wall = (g.y - cy < 0) || (g.y - cy >= p.ny);
+            if (from_wall) {
+                f[i] = PairIO<S>::ld2(A.p[i] + g.s0);
+            } else {
+                const int r = g.s0 + g.oy[1 - cy] + g.oz[1 - cz];
+                if (cx == 0)
+                    f[i] = PairIO<S>::ld2(A.p[o] + r);
+                else
+                    f[i] = PairIO<S>::ld11(A.p[o] + (r + g.ox0[1 - cx]), A.p[o] + (r + 1 + g.ox1[1 - cx]));
+            }
+        }
+    });
+}
+
+template <class L, class S, bool ODD, bool WALL>
+__device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, const f2 *f) {
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int o = opp(i);
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        if (!ODD) {
+            PairIO<S>::st2(A.p[o] + g.s0, f[i]);
+        } else {
+            bool to_wall = false;
+            if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
+            if (to_wall) {
+                PairIO<S>::st2(A.p[o] + g.s0, f[i]);
+            } else {
+                const int r = g.s0 + g.oy[1 + cy] + g.oz[1 + cz];
+                if (cx == 0)
+                    PairIO<S>::st2(A.p[i] + r, f[i]);
+                else
+                    PairIO<S>::st11(A.p[i] + (r + g.ox0[1 + cx]), A.p[i] + (r + 1 + g.ox1[1 + cx]), f[i]);
+            }
+        }
+    });
+}
+
+__device__ __forceinline__ float2 ldg2(const float *a) { return __ldg(reinterpret_cast<const float2 *>(a)); }
+
+// Force densities of the two cells; pc points at psi of cell x0 (an even padded index).
+template <class L>
+__device__ __forceinline__ void force_pair(const KParams &p, const float *__restrict__ pc, f2 F[3]) {
+    const int sy = p.px, sz = p.px * p.py;
+    // psi of both cells at offset (cx, cy, cz), from three float2 per row
+    auto at = [&](int cx, int cy, int cz) -> f2 {
+        const float *r = pc + cy * sy + cz * sz;
+        const float2 c = ldg2(r);
+        if (cx == 0) return f2(c);
+        if (cx < 0) return f2(ldg2(r - 2).y, c.x);
+        return f2(c.y, ldg2(r + 2).x);
+    };
+    const f2 psi0 = at(0, 0, 0);
+    const f2 two_psi0 = psi0 + psi0;
+    f2 m1[3] = {f2(0), f2(0), f2(0)};
+    f2 m2[3][3] = {{f2(0), f2(0), f2(0)}, {f2(0), f2(0), f2(0)}, {f2(0), f2(0), f2(0)}};
+    Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
+        constexpr int i = 2 * decltype(kc)::value + 1;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const f2 pa = at(cx, cy, cz), pb = at(-cx, -cy, -cz);
+        const f2 dif = pa - pb;
+        const f2 sym = (pa + pb) - two_psi0;
+        constexpr double w3 = 3.0 * L::w(i), w9 = 9.0 * L::w(i);
+        constexpr int c[3] = {cx, cy, cz};
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            if (c[a] != 0) m1[a] = mad(f2(w3 * c[a]), dif, m1[a]);
+#pragma unroll
+            for (int b = a; b < L::D; ++b) {
+                const double coef = w9 * (c[a] * c[b] - (a == b ? 1.0 / 3.0 : 0.0));
+                if (coef != 0.0) m2[a][b] = mad(f2(coef), sym, m2[a][b]);
+            }
+        }
+    });
+    f2 tr = m2[0][0] + m2[1][1];
+    if (L::D == 3) tr += m2[2][2];
+    const Phys<float> &q = p.f;
+    const f2 cA = f2(q.A_m1m2), cM = mad(f2(-q.G), psi0, f2(q.B_m1tr) * tr);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+        f2 m21 = f2(0);
+#pragma unroll
+        for (int b = 0; b < L::D; ++b) m21 = mad(a <= b ? m2[a][b] : m2[b][a], m1[b], m21);
+        F[a] = mad(cM, m1[a], mad(cA, m21, f2(q.fext[a])));
+    }
+    if (L::D == 2) F[2] = f2(0);
+}
+
+// psi of one cell into the ghost layer (boundary cells only).
+template <class L>
+__device__ __forceinline__ void psi_ghosts(const KParams &p, float *psi, int x, int y, int z, float v) {
+    int xs[3], ys[3], zs[3];
+    int nxs = 1, nys = 1, nzs = 1;
+    xs[0] = x;
+    if (x == p.nx - 1) xs[nxs++] = -1;
+    if (x == 0) xs[nxs++] = p.nx;
+    ys[0] = y;
+    if (p.wall_y) {
+        if (y == 0) ys[nys++] = -1;
+        if (y == p.ny - 1) ys[nys++] = p.ny;
+    } else {
+        if (y == p.ny - 1) ys[nys++] = -1;
+        if (y == 0) ys[nys++] = p.ny;
+    }
+    zs[0] = z;
+    if (L::D == 3) {
+        if (z == p.nz - 1) zs[nzs++] = -1;
+        if (z == 0) zs[nzs++] = p.nz;
+    }
+    for (int c = 0; c < nzs; ++c)
+        for (int b = 0; b < nys; ++b)
+            for (int a = (c == 0 && b == 0) ? 1 : 0; a < nxs; ++a) psi[psi_index(p, xs[a], ys[b], zs[c])] = v;
+}
+
+// psi of Eq. Interaction_Potential for two cells; raises the device flags on domain errors.
+__device__ __forceinline__ f2 psi_pair_of(const KParams &p, f2 rho) {
+    const Phys<float> &q = p.f;
+    f2 pr;
+    if (p.eos_kind == 0) {
+        const f2 br = f2(q.pr_b) * rho;
+        const f2 d1 = f2(1.0f) - br, d2 = mad(br, f2(2.0f) - br, f2(1.0f));
+        pr = fdiv(rho * mad(f2(q.pr_RT), d2, f2(-q.pr_aalpha) * rho * d1), d1 * d2);
+    } else {
+        const f2 sr = f2(sqrtf(rho.v.x), sqrtf(rho.v.y));
+        const f2 r2 = rho * rho;
+        const float rv = q.pe_rv, rl = q.pe_rl, sv = q.pe_sv;
+        // 2 r^3 + (rv - 2 rl) r^2 - 3 sv r^2.5 + 2 sv rl r^1.5 + sv rl^2 r^0.5
+        f2 poly = mad(f2(2.0f), rho, f2(rv - 2.0f * rl)) * r2;
+        poly = mad(mad(f2(-3.0f * sv), r2, mad(f2(2.0f * sv * rl), rho, f2(sv * rl * rl))), sr, poly);
+        pr = f2(q.pe_P) * poly;
+    }
+    const f2 arg = f2(2.0f * q.inv_G) * mad(f2(q.p_scale), pr, f2(-1.0f / 3.0f) * rho);
+    float out[2];
+    const float rr[2] = {rho.v.x, rho.v.y}, aa[2] = {arg.v.x, arg.v.y};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(rr[c] > 0.0f) || !(rr[c] < INFINITY)) {
+            atomicOr(p.flags, FLAG_NONFINITE);
+            out[c] = 0.0f;
+        } else if (!(aa[c] >= 0.0f)) {
+            atomicOr(p.flags, FLAG_PSI_DOMAIN);
+            out[c] = 0.0f;
+        } else {
+            out[c] = sqrtf(aa[c]);
+        }
+    }
+    return f2(out[0], out[1]);
+}
+
+template <class L, class S, bool ODD, bool WALL>
+__device__ __forceinline__ void psi_pair_body(const KParams &p, const Planes<S> &A, float *psi, const GeoPair &g) {
+    f2 f[L::Q];
+    load_pair<L, S, ODD, WALL>(p, A, g, f);
+    f2 rho = f[0];
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) rho += f[i];
+    if (Store<S>::SHIFT) rho += f2(p.f.rho_ref);   // sum_i w_i rho_ref = rho_ref
+    const f2 v = psi_pair_of(p, rho);
+    float *dst = psi + psi_index(p, g.x0, g.y, g.z);
+    *reinterpret_cast<float2 *>(dst) = v.v;
+    const bool by = g.y == 0 || g.y == p.ny - 1, bz = L::D == 3 && (g.z == 0 || g.z == p.nz - 1);
+    if (by || bz || g.x0 == 0) psi_ghosts<L>(p, psi, g.x0, g.y, g.z, v.v.x);
+    if (by || bz || g.x0 + 1 == p.nx - 1) psi_ghosts<L>(p, psi, g.x0 + 1, g.y, g.z, v.v.y);
+}
+
+template <class L, class S, bool ODD>
+__global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float *__restrict__ psi) {
+    GeoPair g;
+    if (!make_geo_pair(p, g)) return;
+    if (ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1))
+        psi_pair_body<L, S, ODD, true>(p, A, psi, g);
+    else
+        psi_pair_body<L, S, ODD, false>(p, A, psi, g);
+}
+
+#ifndef PLB_PAIR_MINB
+#define PLB_PAIR_MINB 2
+#endif
+
+template <class L, class S, int MRT, bool ODD, bool WALL>
+__device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes<S> &A, const float *__restrict__ psi,
+                                                  const GeoPair &g) {
+    f2 f[L::Q];
+    load_pair<L, S, ODD, WALL>(p, A, g, f);
+    f2 F[3];
+    force_pair<L>(p, psi + psi_index(p, g.x0, g.y, g.z), F);
+    collide_fast<L, MRT, Store<S>::SHIFT, f2>(p, f, F);
+    store_pair<L, S, ODD, WALL>(p, A, g, f);
+}
+
+template <class L, class S, int MRT, bool ODD>
+__global__ void __launch_bounds__(256, PLB_PAIR_MINB) k_collide_pair(KParams p, Planes<S> A,
+                                                                    const float *__restrict__ psi) {
+    GeoPair g;
+    if (!make_geo_pair(p, g)) return;
+    if (ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1))
+        collide_pair_body<L, S, MRT, ODD, true>(p, A, psi, g);
+    else
+        collide_pair_body<L, S, MRT, ODD, false>(p, A, psi, g);
+}
+
+}  // namespace plb

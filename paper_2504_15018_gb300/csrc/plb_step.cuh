@@ -133,47 +133,77 @@ template <class L> struct RowParity {
     }
 };
 
+// acc += c v for c in {-1, 0, 1} known at compile time (no multiplication).
+template <int C, class T> __device__ __forceinline__ void add_c(T &acc, const T &v) {
+    if (C > 0) acc += v;
+    if (C < 0) acc -= v;
+}
+template <int CX, int CY, int CZ, class T> __device__ __forceinline__ T dot_c(const T *v) {
+    T r = T(0);
+    bool first = true;
+    auto term = [&](int c, const T &x) {
+        if (c == 0) return;
+        if (first) {
+            r = c > 0 ? x : -x;
+            first = false;
+        } else {
+            r = c > 0 ? r + x : r - x;
+        }
+    };
+    term(CX, v[0]);
+    term(CY, v[1]);
+    term(CZ, v[2]);
+    return r;
+}
+
 // In place: stored values h -> post-collision stored values.  SHIFT: h_i = f_i - w_i rho_ref
 // (FP16 storage); then rho = sum h + rho_ref (sum_i w_i = 1), j = sum c_i h_i
-// (sum_i w_i c_i = 0), feq_i - f_i = w_i (rho t2 - rho_ref) - h_i, and the update adds to h.
+// (sum_i w_i c_i = 0), f_i - feq_i = h_i - w_i (rho t2 - rho_ref), and the update adds to h.
+// T is double, float, or f2 (two cells at once).
 template <class L, int MRT, bool SHIFT, class T>
 __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3]) {
-    const Phys<T> &q = phys<T>(p);
-    T rho = f[0], j[3] = {0, 0, 0};
+    using R = typename ScalarOf<T>::type;
+    const Phys<R> &q = phys<R>(p);
+    T rho = f[0], j[3] = {T(0), T(0), T(0)};
     Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
         constexpr int i = 2 * decltype(kc)::value + 1;
         const T a = f[i] - f[i + 1];
         rho += f[i] + f[i + 1];
-        if (L::cx(i)) j[0] = mad((T)L::cx(i), a, j[0]);
-        if (L::cy(i)) j[1] = mad((T)L::cy(i), a, j[1]);
-        if (L::cz(i)) j[2] = mad((T)L::cz(i), a, j[2]);
+        add_c<L::cx(i)>(j[0], a);
+        add_c<L::cy(i)>(j[1], a);
+        add_c<L::cz(i)>(j[2], a);
     });
-    if (SHIFT) rho += q.rho_ref;
-    const T irho = fdiv((T)1, rho);
-    const T u[3] = {mad((T)0.5, F[0], j[0]) * irho, mad((T)0.5, F[1], j[1]) * irho, mad((T)0.5, F[2], j[2]) * irho};
+    if (SHIFT) rho += T(q.rho_ref);
+    const T irho = fdiv(T(1), rho);
+    const T u[3] = {mad(T(0.5), F[0], j[0]) * irho, mad(T(0.5), F[1], j[1]) * irho, mad(T(0.5), F[2], j[2]) * irho};
     const T om = omega_of<T>(p, rho);
-    const T Aeq = (T)1 - (T)1.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const T uF3 = (T)3 * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
-    const T kguo = (T)1 - (T)0.5 * om;
+    const T nom = -om;
+    const T Aeq = mad(T(-1.5), mad(u[0], u[0], mad(u[1], u[1], u[2] * u[2])), T(1));
+    const T nuF3 = T(-3) * mad(u[0], F[0], mad(u[1], F[1], u[2] * F[2]));
+    const T kguo = mad(T(-0.5), om, T(1));
+    const T nrref = T(-q.rho_ref);
     T g[L::Q];
-    Unroll<0, L::Q>::run([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        T cu = 0, cF = 0;
-        if (cx) { cu += (T)cx * u[0]; cF += (T)cx * F[0]; }
-        if (cy) { cu += (T)cy * u[1]; cF += (T)cy * F[1]; }
-        if (cz) { cu += (T)cz * u[2]; cF += (T)cz * F[2]; }
-        const T wi = (T)L::w(i);
-        const T t2 = mad(cu, mad((T)4.5, cu, (T)3), Aeq);         // feq / (w rho)
-        const T t4 = mad(cF, mad((T)9, cu, (T)3), -uF3);         // Ft / w
-        const T d = SHIFT ? mad(wi, mad(rho, t2, -q.rho_ref), -f[i])   // feq - f
-                          : mad(wi * rho, t2, -f[i]);
+    // one direction: t2 = feq / (w rho), t4 = Ft / w
+    auto update = [&](int i, double w, const T &t2, const T &t4) {
+        const T dn = SHIFT ? mad(T(-w), mad(rho, t2, nrref), f[i])    // f - feq
+                           : mad(T(-w) * rho, t2, f[i]);
         if (!MRT) {
-            f[i] = mad(kguo * wi, t4, mad(om, d, f[i]));
+            f[i] = mad(kguo * T(w), t4, mad(nom, dn, f[i]));
         } else {
-            g[i] = mad((T)0.5 * wi, t4, -d);                     // f - feq + Ft/2
-            f[i] = mad(-om, g[i], mad(wi, t4, f[i]));             // BGK part with Ft
+            g[i] = mad(T(0.5 * w), t4, dn);                      // f - feq + Ft/2
+            f[i] = mad(nom, g[i], mad(T(w), t4, f[i]));           // BGK part with Ft
         }
+    };
+    update(0, L::w(0), Aeq, nuF3);
+    // opposite pair (i, i + 1): c_{i+1} = -c_i, the first non-zero component of c_i is +1
+    Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
+        constexpr int i = 2 * decltype(kc)::value + 1;
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const T cu = dot_c<cx, cy, cz>(u);
+        const T cF = dot_c<cx, cy, cz>(F);
+        constexpr double w = L::w(i);
+        update(i, w, mad(cu, mad(T(4.5), cu, T(3)), Aeq), mad(cF, mad(T(9), cu, T(3)), nuF3));
+        update(i + 1, w, mad(cu, mad(T(4.5), cu, T(-3)), Aeq), mad(cF, mad(T(9), cu, T(-3)), nuF3));
     });
     if (MRT) {
         constexpr int NP = (L::Q - 1) / 2;
@@ -187,29 +217,29 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
         Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
             constexpr int k = decltype(kk)::value;
             constexpr bool ev = RowParity<L>::even(k);
-            T m = ev ? (T)Ghosts<L>::row(k, 0) * g[0] : (T)0;
+            T m = ev ? T(Ghosts<L>::row(k, 0)) * g[0] : T(0);
             Unroll<0, NP>::run([&](auto qc) {
                 constexpr int r = decltype(qc)::value;
                 constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
-                if (c != 0.0) m = mad((T)c, ev ? gs[r] : ga[r], m);
+                if (c != 0.0) m = mad(T(c), ev ? gs[r] : ga[r], m);
             });
-            Ak[k] = (q.s_rate[Ghosts<L>::kind(k)] - om) * (T)(1.0 / row_norm2<L>(k)) * m;
+            Ak[k] = (T(q.s_rate[Ghosts<L>::kind(k)]) - om) * (T(1.0 / row_norm2<L>(k)) * m);
         });
-        T e0 = 0;
+        T e0 = T(0);
         Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            if (RowParity<L>::even(k) && Ghosts<L>::row(k, 0) != 0.0) e0 = mad((T)Ghosts<L>::row(k, 0), Ak[k], e0);
+            if (RowParity<L>::even(k) && Ghosts<L>::row(k, 0) != 0.0) e0 = mad(T(Ghosts<L>::row(k, 0)), Ak[k], e0);
         });
         f[0] -= e0;
         Unroll<0, NP>::run([&](auto qc) {
             constexpr int r = decltype(qc)::value;
-            T E = 0, O = 0;
+            T E = T(0), O = T(0);
             Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
                 constexpr int k = decltype(kk)::value;
                 constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
                 if (c != 0.0) {
-                    if (RowParity<L>::even(k)) E = mad((T)c, Ak[k], E);
-                    else O = mad((T)c, Ak[k], O);
+                    if (RowParity<L>::even(k)) E = mad(T(c), Ak[k], E);
+                    else O = mad(T(c), Ak[k], O);
                 }
             });
             f[2 * r + 1] -= E + O;
