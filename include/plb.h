@@ -186,6 +186,70 @@ int plb_solve_params(const plb_eos_params *eos, double *rho_v, double *rho_l, do
  * out = {C_L, C_T, C_M, C_U, C_VF, C_gamma, rho_v, tau_v, gamma_lat, pc_over_rhoc3, kappa}. */
 int plb_si_convert(const double si[6], const double lat[3], double xi, double out[11]);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent lattices of one lattice type, storage precision and collision (sizes,
+ * EOS, tau, eps, kappa, walls and forces may differ per instance) advanced together by one
+ * persistent kernel launch per plb_batch_step call: every step is a psi pass over all
+ * instances, a grid barrier, the fused force/collide/stream pass, and another barrier
+ * (the same per-cell update as plb_step, Sec. II of the paper).  Work is split into tiles of
+ * whole rows; the tile size and resident blocks per SM are set by plb_batch_autotune or
+ * plb_batch_configure.  The grid barrier waits a bounded time: a wait that runs out sets a
+ * device error word, the kernel returns, and plb_batch_status reports PLB_ETIMEOUT. */
+typedef struct plb_batch_state plb_batch_t;
+
+typedef struct plb_instance {
+    int dims[3];
+    plb_eos_params eos;
+    double tau, G, eps;
+    plb_opts opts;         /* precision and collision must match across a batch */
+} plb_instance;
+
+/* Bytes of device workspace for a batch (0 on invalid arguments). */
+size_t plb_batch_workspace_bytes(int lattice, int n, const plb_instance *inst);
+
+/* Creates a batch of n instances over a caller-owned, 256-byte aligned device workspace and
+ * stream.  On a non-default stream each step count is captured once as a CUDA graph and
+ * replayed.  Errors: PLB_EINVAL, PLB_ENOMEM, PLB_EUNSUPPORTED, PLB_ECUDA. */
+int plb_batch_create(int lattice, int n, const plb_instance *inst, void *dev_workspace, size_t ws_bytes,
+                     void *cuda_stream, plb_batch_t **out);
+void plb_batch_destroy(plb_batch_t *b);
+
+/* Instance k as a read-only lattice handle for plb_moments, plb_reduce, plb_get_populations,
+ * plb_get_state, plb_status and plb_time (plb_step / plb_init / plb_set_* refuse it; do not
+ * destroy it).  NULL for a bad index. */
+plb_t *plb_batch_instance(plb_batch_t *b, int k);
+
+/* f = f^eq(rho0, u0) on instance k (as plb_init). */
+int plb_batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0);
+
+/* Advances every instance by nsteps steps in one persistent launch.  Asynchronous. */
+int plb_batch_step(plb_batch_t *b, int nsteps);
+
+/* Synchronises; PLB_ETIMEOUT if a grid barrier gave up, else the first instance's
+ * PLB_EPSI_DOMAIN / PLB_ENONFINITE, else PLB_OK. */
+int plb_batch_status(plb_batch_t *b);
+
+/* Clears a recorded barrier timeout. */
+int plb_batch_reset_error(plb_batch_t *b);
+
+/* Tile size in cells (rows of a tile = tile_cells / nx, at least 1), resident 256-thread
+ * blocks per SM, and the barrier's polling limit (0 keeps the default, about a second or more).
+ * A non-positive tile_cells or blocks_per_sm keeps the current value. */
+int plb_batch_configure(plb_batch_t *b, int tile_cells, int blocks_per_sm, unsigned spin_limit);
+
+/* Times steps_per_candidate steps for every tile size in {1024, ..., 16384} cells and 1 or 2
+ * blocks per SM, keeps the fastest, and reports it (any output may be NULL; best_ms is per
+ * step).  The timed steps advance the batch. */
+int plb_batch_autotune(plb_batch_t *b, int steps_per_candidate, int *tile_cells, int *blocks_per_sm, double *best_ms);
+
+/* Test hook for failure detection: the next plb_batch_step launch's barriers wait for count
+ * blocks more than are launched, so every wait runs out (bounded by the polling limit) and
+ * plb_batch_status reports PLB_ETIMEOUT.  Nothing faults or hangs. */
+int plb_batch_withhold_arrivals(plb_batch_t *b, unsigned count);
+
+/* Steps taken by the batch. */
+long long plb_batch_time(const plb_batch_t *b);
+
 /* Allocation-free stepping, for callers that cannot allocate device memory: a plugin
  * that lives inside another framework's memory arena and only receives the buffers it
  * works on, or a real-time loop in which cudaMalloc (which may synchronise the device) is

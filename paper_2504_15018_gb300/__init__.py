@@ -58,6 +58,11 @@ class plb_opts(ctypes.Structure):
                 ("body_force", ctypes.c_double * 3)]
 
 
+class plb_instance(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 3), ("eos", plb_eos_params), ("tau", ctypes.c_double),
+                ("G", ctypes.c_double), ("eps", ctypes.c_double), ("opts", plb_opts)]
+
+
 _DP = ctypes.POINTER(ctypes.c_double)
 _IP = ctypes.POINTER(ctypes.c_int)
 _VP = ctypes.c_void_p
@@ -88,6 +93,19 @@ _SIGNATURES = {
     "plb_step_pairs_static": (ctypes.c_int, [ctypes.c_int, _IP, ctypes.POINTER(plb_eos_params), ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(plb_opts), _VP,
                                              ctypes.c_int, _VP]),
+    "plb_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(plb_instance)]),
+    "plb_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(plb_instance), _VP, ctypes.c_size_t,
+                                        _VP, ctypes.POINTER(_VP)]),
+    "plb_batch_destroy": (None, [_VP]),
+    "plb_batch_instance": (_VP, [_VP, ctypes.c_int]),
+    "plb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+    "plb_batch_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "plb_batch_status": (ctypes.c_int, [_VP]),
+    "plb_batch_reset_error": (ctypes.c_int, [_VP]),
+    "plb_batch_configure": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "plb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
+    "plb_batch_withhold_arrivals": (ctypes.c_int, [_VP, ctypes.c_uint]),
+    "plb_batch_time": (ctypes.c_longlong, [_VP]),
     "plb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -247,6 +265,65 @@ def plb_step_pairs_static(lattice: int, dims, eos: plb_eos_params, tau: float, G
                                        int(npairs), _VP(cuda_stream)))
 
 
+def plb_batch_workspace_bytes(lattice: int, instances) -> int:
+    arr = (plb_instance * len(instances))(*instances)
+    return lib().plb_batch_workspace_bytes(lattice, len(instances), arr)
+
+
+def plb_batch_create(lattice: int, instances, dev_workspace: int, ws_bytes: int, cuda_stream: int):
+    arr = (plb_instance * len(instances))(*instances)
+    b = _VP()
+    _check(lib().plb_batch_create(lattice, len(instances), arr, _VP(dev_workspace), ws_bytes, _VP(cuda_stream),
+                                  ctypes.byref(b)))
+    return b
+
+
+def plb_batch_destroy(b):
+    lib().plb_batch_destroy(b)
+
+
+def plb_batch_instance(b, k: int):
+    h = lib().plb_batch_instance(b, int(k))
+    if not h:
+        raise PlbError(PLB_EINVAL, f"no instance {k}")
+    return _VP(h)
+
+
+def plb_batch_init(b, k: int, rho0, u0=None):
+    _check(lib().plb_batch_init(b, int(k), _dptr(rho0), _dptr(u0)))
+
+
+def plb_batch_step(b, nsteps: int):
+    _check(lib().plb_batch_step(b, int(nsteps)))
+
+
+def plb_batch_status(b):
+    _check(lib().plb_batch_status(b))
+
+
+def plb_batch_reset_error(b):
+    _check(lib().plb_batch_reset_error(b))
+
+
+def plb_batch_configure(b, tile_cells: int = 0, blocks_per_sm: int = 0, spin_limit: int = 0):
+    _check(lib().plb_batch_configure(b, int(tile_cells), int(blocks_per_sm), int(spin_limit)))
+
+
+def plb_batch_autotune(b, steps_per_candidate: int = 5):
+    tc, bps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().plb_batch_autotune(b, int(steps_per_candidate), ctypes.byref(tc), ctypes.byref(bps),
+                                    ctypes.byref(ms)))
+    return tc.value, bps.value, ms.value
+
+
+def plb_batch_withhold_arrivals(b, count: int):
+    _check(lib().plb_batch_withhold_arrivals(b, int(count)))
+
+
+def plb_batch_time(b) -> int:
+    return lib().plb_batch_time(b)
+
+
 # ------------------------------------------------------------------- helpers
 
 def pr_eos(T_over_Tc: float, a: float = 2.0 / 49.0, b: float = 2.0 / 21.0, R: float = 1.0, omega: float = 0.327,
@@ -271,6 +348,83 @@ def make_opts(**kw) -> plb_opts:
         else:
             setattr(o, k, v)
     return o
+
+
+def make_instance(dims, eos: plb_eos_params, tau: float = 1.0, G: float = -1.0, eps: float = 2.0,
+                  opts: plb_opts | None = None) -> plb_instance:
+    inst = plb_instance()
+    d = (list(dims) + [1, 1])[:3]
+    for a in range(3):
+        inst.dims[a] = int(d[a])
+    inst.eos = eos
+    inst.tau, inst.G, inst.eps = tau, G, eps
+    inst.opts = opts if opts is not None else plb_default_opts()
+    return inst
+
+
+class Batch:
+    """A batch of independent lattices advanced by one persistent launch per step call."""
+
+    def __init__(self, lattice: int, instances, device: str = "cuda", stream=None):
+        import torch
+        self.lattice = lattice
+        self.instances = list(instances)
+        nbytes = plb_batch_workspace_bytes(lattice, self.instances)
+        if nbytes == 0:
+            raise PlbError(PLB_EINVAL, "bad batch description")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        aligned = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.ws.device)
+        self.b = plb_batch_create(lattice, self.instances, aligned, nbytes, self.stream.cuda_stream)
+        self.Q = 9 if lattice == PLB_D2Q9 else 19
+        self.D = 2 if lattice == PLB_D2Q9 else 3
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            try:
+                plb_batch_destroy(b)
+            except Exception:
+                pass
+            self.b = None
+
+    def __len__(self):
+        return len(self.instances)
+
+    def cells(self, k: int) -> int:
+        d = self.instances[k].dims
+        return d[0] * d[1] * d[2]
+
+    def init(self, k: int, rho0, u0=None):
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
+        u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        plb_batch_init(self.b, k, rho0, u0)
+
+    def step(self, n: int = 1):
+        plb_batch_step(self.b, n)
+
+    def status(self):
+        plb_batch_status(self.b)
+
+    def autotune(self, steps_per_candidate: int = 5):
+        return plb_batch_autotune(self.b, steps_per_candidate)
+
+    def configure(self, tile_cells: int = 0, blocks_per_sm: int = 0, spin_limit: int = 0):
+        plb_batch_configure(self.b, tile_cells, blocks_per_sm, spin_limit)
+
+    def populations(self, k: int) -> np.ndarray:
+        f = np.zeros((self.Q, self.cells(k)))
+        plb_get_populations(plb_batch_instance(self.b, k), f)
+        return f
+
+    def moments(self, k: int):
+        n = self.cells(k)
+        rho, u, p = np.zeros(n), np.zeros((self.D, n)), np.zeros(n)
+        plb_moments(plb_batch_instance(self.b, k), rho, u, p)
+        return rho, u, p
+
+    def reduce(self, k: int, what: int, lo=None, hi=None):
+        return plb_reduce(plb_batch_instance(self.b, k), what, lo, hi)
 
 
 class Lattice:

@@ -28,6 +28,7 @@ UNITS = [
     ("plb_kern_fp16.cu", []),
     ("plb_params.cpp", []),
     ("plb_noalloc.cu", []),
+    ("plb_batch.cu", []),
 ]
 
 

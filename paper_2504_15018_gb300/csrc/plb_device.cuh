@@ -110,27 +110,40 @@ template <class L> __host__ __device__ constexpr double row_norm2(int k) {
 // Arithmetic in double for FP64 storage, float otherwise.  ld / st move one stored value
 // to / from arithmetic precision without any shift; with SHIFT (FP16 storage) the stored
 // value is the deviation f_i - w_i rho_ref, and the kernels account for the shift.
+// Load policies.  LdStream: populations streamed with evict-first hints, psi through the
+// read-only path; right for kernels in which nothing read is written by another block.
+// LdCoherent: every load through L2 only, for the persistent batch kernel, whose blocks read
+// across grid barriers what other SMs wrote in the same launch (L1 is not coherent).
+struct LdStream {
+    template <class U> __device__ __forceinline__ static U ld(const U *a) { return __ldcs(a); }
+    template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldg(a); }
+};
+struct LdCoherent {
+    template <class U> __device__ __forceinline__ static U ld(const U *a) { return __ldcg(a); }
+    template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldcg(a); }
+};
+
 template <class S> struct Store;
 template <> struct Store<double> {
     using T = double;
     using PsiT = double;
     static constexpr bool SHIFT = false;
-    __device__ static T ld(const double *a) { return __ldcs(a); }
+    template <class Pol = LdStream> __device__ static T ld(const double *a) { return Pol::ld(a); }
     __device__ static void st(double *a, T v) { __stcs(a, v); }
 };
 template <> struct Store<float> {
     using T = float;
     using PsiT = float;
     static constexpr bool SHIFT = false;
-    __device__ static T ld(const float *a) { return __ldcs(a); }
+    template <class Pol = LdStream> __device__ static T ld(const float *a) { return Pol::ld(a); }
     __device__ static void st(float *a, T v) { __stcs(a, v); }
 };
 template <> struct Store<__half> {
     using T = float;
     using PsiT = float;
     static constexpr bool SHIFT = true;
-    __device__ static T ld(const __half *a) {
-        return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short *>(a))));
+    template <class Pol = LdStream> __device__ static T ld(const __half *a) {
+        return __half2float(__ushort_as_half(Pol::ld(reinterpret_cast<const unsigned short *>(a))));
     }
     __device__ static void st(__half *a, T v) {
         __stcs(reinterpret_cast<unsigned short *>(a), __half_as_ushort(__float2half_rn(v)));

@@ -44,3 +44,32 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
 const Launchers *launchers_for_precision(int lattice, int precision);
 
 }  // namespace plb
+
+#include "plb_launch.h"
+
+// A lattice handle: its parameters and the device regions it works on.  plb_create points
+// the regions into the caller's workspace; a batch points them into its arena.
+struct plb_state {
+    int lattice;
+    int dims[3];
+    plb_opts opts;
+    plb_eos_params eos;
+    double tau, G, eps;
+    double rho_v, rho_l, p0;   // coexistence densities of the EOS (p_scale = 1)
+    plb::Layout lay;
+    plb::KParams kp;
+    const plb::Launchers *L;
+    char *ws;
+    char *pops, *psi;          // population store, padded psi field
+    double *partials, *out;    // reduction partials (lay.max_blocks x 4), final values (4)
+    double *staging;           // host<->device staging (lay.chunk cells)
+    cudaStream_t stream;
+    long long t;
+    int odd;
+    int view;                  // 1: an instance of a batch (stepped only by plb_batch_step)
+};
+
+namespace plb {
+// f = f^eq(rho0, u0) on every cell of h (the body of plb_init).
+int init_state(plb_state *h, const double *rho0, const double *u0);
+}  // namespace plb

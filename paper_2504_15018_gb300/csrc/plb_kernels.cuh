@@ -6,6 +6,7 @@
 
 #include "plb_device.cuh"
 #include "plb_launch.h"
+#include "plb_batch.cuh"
 #include "plb_pair.cuh"
 #include "plb_step.cuh"
 
@@ -267,8 +268,11 @@ template <class L, class S> struct Launch {
         k_reduce<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, what, lo[0], lo[1], lo[2],
                                                 hi[0], hi[1], hi[2], partials);
     }
+    static const void *batch_bgk() { return reinterpret_cast<const void *>(&k_batch<L, S, 0>); }
+    static const void *batch_mrt() { return reinterpret_cast<const void *>(&k_batch<L, S, 1>); }
     static constexpr Launchers table() {
-        return Launchers{&init, &psi, {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce};
+        return Launchers{&init,     &psi,    {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce,
+                         {&batch_bgk, &batch_mrt}};
     }
 };
 

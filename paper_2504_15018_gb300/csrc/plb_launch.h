@@ -38,6 +38,34 @@ struct KParams {
     unsigned *flags;
 };
 
+// One instance of a batch, as the persistent kernel sees it (device memory).
+struct BatchInst {
+    KParams kp;            // kp.flags points at the instance's flags
+    void *pl[19];          // population planes
+    void *psi;             // padded psi field
+    int odd;               // AA parity at the start of the launch (the kernel flips it at the end)
+    int pair;              // 1: two cells per thread
+    int upr;               // work units per row: nx / 2 (pair) or nx
+    int pad;
+};
+// A tile: rows y0 <= y < y1 of plane z of one instance.
+struct BatchTile {
+    int inst, z, y0, y1;
+};
+// Grid barrier state (device memory, zeroed at creation).
+struct GridBar {
+    unsigned count, gen, err, pad;
+};
+// Launch parameters of the persistent kernel.
+struct BatchLaunch {
+    BatchInst *insts;
+    const BatchTile *tiles;
+    int ninst, ntiles, nsteps;
+    GridBar *bar;
+    unsigned spin_limit;     // bounded wait: polls of the barrier before giving up
+    unsigned expected;       // blocks the barrier waits for (gridDim.x unless testing a timeout)
+};
+
 struct Launchers {
     void (*init)(const KParams &, void *A, const double *rho0, const double *u0, long long c0, long long cn,
                  cudaStream_t);
@@ -49,6 +77,8 @@ struct Launchers {
     void (*set_pops)(const KParams &, void *A, const double *in, long long c0, long long cn, cudaStream_t);
     void (*reduce)(const KParams &, const void *A, const void *psi, int odd, int what, const int lo[3],
                    const int hi[3], double *partials, int nblocks, cudaStream_t);
+    // persistent batch kernel [BGK, MRT]: returns its entry point for launch / occupancy queries
+    const void *(*batch_kernel[2])();
 };
 
 // Defined in plb_kern_fp64.cu / plb_kern_fp32.cu / plb_kern_fp16.cu; lattice 0 = D2Q9, 1 = D3Q19.

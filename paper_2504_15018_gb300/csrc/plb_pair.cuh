@@ -15,8 +15,12 @@ namespace plb {
 
 template <class S> struct PairIO;
 template <> struct PairIO<float> {
-    __device__ static f2 ld2(const float *a) { return f2(__ldcs(reinterpret_cast<const float2 *>(a))); }
-    __device__ static f2 ld11(const float *a0, const float *a1) { return f2(__ldcs(a0), __ldcs(a1)); }
+    template <class Pol> __device__ static f2 ld2(const float *a) {
+        return f2(Pol::ld(reinterpret_cast<const float2 *>(a)));
+    }
+    template <class Pol> __device__ static f2 ld11(const float *a0, const float *a1) {
+        return f2(Pol::ld(a0), Pol::ld(a1));
+    }
     __device__ static void st2(float *a, f2 v) { __stcs(reinterpret_cast<float2 *>(a), v.v); }
     __device__ static void st11(float *a0, float *a1, f2 v) {
         __stcs(a0, v.v.x);
@@ -24,14 +28,14 @@ template <> struct PairIO<float> {
     }
 };
 template <> struct PairIO<__half> {
-    __device__ static f2 ld2(const __half *a) {
-        const unsigned int b = __ldcs(reinterpret_cast<const unsigned int *>(a));
+    template <class Pol> __device__ static f2 ld2(const __half *a) {
+        const unsigned int b = Pol::ld(reinterpret_cast<const unsigned int *>(a));
         __half2 h;
         *reinterpret_cast<unsigned int *>(&h) = b;
         return f2(__half22float2(h));
     }
-    __device__ static f2 ld11(const __half *a0, const __half *a1) {
-        return f2(Store<__half>::ld(a0), Store<__half>::ld(a1));
+    template <class Pol> __device__ static f2 ld11(const __half *a0, const __half *a1) {
+        return f2(Store<__half>::ld<Pol>(a0), Store<__half>::ld<Pol>(a1));
     }
     __device__ static void st2(__half *a, f2 v) {
         const __half2 h = __floats2half2_rn(v.v.x, v.v.y);
@@ -50,11 +54,10 @@ struct GeoPair {
     int ox0[3], ox1[3], oy[3], oz[3];
 };
 
-__device__ __forceinline__ bool make_geo_pair(const KParams &p, GeoPair &g) {
-    g.x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    g.y = blockIdx.y * blockDim.y + threadIdx.y;
-    g.z = blockIdx.z;
-    if (g.x0 >= p.nx || g.y >= p.ny) return false;
+__device__ __forceinline__ void geo_pair_at(const KParams &p, int x0, int y, int z, GeoPair &g) {
+    g.x0 = x0;
+    g.y = y;
+    g.z = z;
     const int row = p.nx, plane = p.nx * p.ny;
     g.s0 = g.x0 + row * (g.y + p.ny * g.z);
     g.ox0[0] = g.x0 > 0 ? -1 : p.nx - 1;
@@ -69,28 +72,35 @@ __device__ __forceinline__ bool make_geo_pair(const KParams &p, GeoPair &g) {
     g.oz[0] = g.z > 0 ? -plane : plane * (p.nz - 1);
     g.oz[1] = 0;
     g.oz[2] = g.z < p.nz - 1 ? plane : -plane * (p.nz - 1);
+}
+
+__device__ __forceinline__ bool make_geo_pair(const KParams &p, GeoPair &g) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return false;
+    geo_pair_at(p, x0, y, blockIdx.z, g);
     return true;
 }
 
-template <class L, class S, bool ODD, bool WALL>
+template <class L, class S, bool ODD, bool WALL, class Pol = LdStream>
 __device__ __forceinline__ void load_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 *f) {
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int o = opp(i);
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         if (!ODD) {
-            f[i] = PairIO<S>::ld2(A.p[i] + g.s0);
+            f[i] = PairIO<S>::template ld2<Pol>(A.p[i] + g.s0);
         } else {
             bool from_wall = false;
             if (WALL && cy != 0) from_wall = (g.y - cy < 0) || (g.y - cy >= p.ny);
             if (from_wall) {
-                f[i] = PairIO<S>::ld2(A.p[i] + g.s0);
+                f[i] = PairIO<S>::template ld2<Pol>(A.p[i] + g.s0);
             } else {
                 const int r = g.s0 + g.oy[1 - cy] + g.oz[1 - cz];
                 if (cx == 0)
-                    f[i] = PairIO<S>::ld2(A.p[o] + r);
+                    f[i] = PairIO<S>::template ld2<Pol>(A.p[o] + r);
                 else
-                    f[i] = PairIO<S>::ld11(A.p[o] + (r + g.ox0[1 - cx]), A.p[o] + (r + 1 + g.ox1[1 - cx]));
+                    f[i] = PairIO<S>::template ld11<Pol>(A.p[o] + (r + g.ox0[1 - cx]),
+                                                        A.p[o] + (r + 1 + g.ox1[1 - cx]));
             }
         }
     });
@@ -120,11 +130,10 @@ __device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A,
     });
 }
 
-__device__ __forceinline__ float2 ldg2(const float *a) { return __ldg(reinterpret_cast<const float2 *>(a)); }
-
 // Force densities of the two cells; pc points at psi of cell x0 (an even padded index).
-template <class L>
+template <class L, class Pol = LdStream>
 __device__ __forceinline__ void force_pair(const KParams &p, const float *__restrict__ pc, f2 F[3]) {
+    auto ldg2 = [](const float *a) { return Pol::ro(reinterpret_cast<const float2 *>(a)); };
     const int sy = p.px, sz = p.px * p.py;
     // psi of both cells at offset (cx, cy, cz), from three float2 per row
     auto at = [&](int cx, int cy, int cz) -> f2 {
@@ -231,10 +240,10 @@ __device__ __forceinline__ f2 psi_pair_of(const KParams &p, f2 rho) {
     return f2(out[0], out[1]);
 }
 
-template <class L, class S, bool ODD, bool WALL>
+template <class L, class S, bool ODD, bool WALL, class Pol = LdStream>
 __device__ __forceinline__ void psi_pair_body(const KParams &p, const Planes<S> &A, float *psi, const GeoPair &g) {
     f2 f[L::Q];
-    load_pair<L, S, ODD, WALL>(p, A, g, f);
+    load_pair<L, S, ODD, WALL, Pol>(p, A, g, f);
     f2 rho = f[0];
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) rho += f[i];
@@ -261,13 +270,13 @@ __global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float 
 #define PLB_PAIR_MINB 2
 #endif
 
-template <class L, class S, int MRT, bool ODD, bool WALL>
+template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream>
 __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes<S> &A, const float *__restrict__ psi,
                                                   const GeoPair &g) {
     f2 f[L::Q];
-    load_pair<L, S, ODD, WALL>(p, A, g, f);
+    load_pair<L, S, ODD, WALL, Pol>(p, A, g, f);
     f2 F[3];
-    force_pair<L>(p, psi + psi_index(p, g.x0, g.y, g.z), F);
+    force_pair<L, Pol>(p, psi + psi_index(p, g.x0, g.y, g.z), F);
     collide_fast<L, MRT, Store<S>::SHIFT, f2>(p, f, F);
     store_pair<L, S, ODD, WALL>(p, A, g, f);
 }

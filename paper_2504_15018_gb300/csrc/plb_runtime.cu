@@ -85,22 +85,6 @@ bool make_layout(int lattice, const int dims[3], int precision, Layout &L) {
 
 }  // namespace plb
 
-struct plb_state {
-    int lattice;
-    int dims[3];
-    plb_opts opts;
-    plb_eos_params eos;
-    double tau, G, eps;
-    double rho_v, rho_l, p0;   // coexistence densities of the EOS (p_scale = 1)
-    plb::Layout lay;
-    plb::KParams kp;
-    const plb::Launchers *L;
-    char *ws;
-    cudaStream_t stream;
-    long long t;
-    int odd;
-};
-
 namespace {
 
 void reduce_final_launch(const double *partials, int nblocks, int is_max, double *out, cudaStream_t st);
@@ -113,9 +97,9 @@ const plb::Launchers *launchers_for(int lattice, int precision) {
     }
 }
 
-void *pops_ptr(plb_t *h) { return h->ws + h->lay.off_pops; }
-void *psi_ptr(plb_t *h) { return h->ws + h->lay.off_psi; }
-double *staging_ptr(plb_t *h) { return reinterpret_cast<double *>(h->ws + h->lay.off_staging); }
+void *pops_ptr(plb_t *h) { return h->pops; }
+void *psi_ptr(plb_t *h) { return h->psi; }
+double *staging_ptr(plb_t *h) { return h->staging; }
 
 int check_launch() {
     cudaError_t e = cudaGetLastError();
@@ -312,6 +296,11 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     h->eps = eps;
     h->lay = lay;
     h->ws = static_cast<char *>(dev_workspace);
+    h->pops = h->ws + lay.off_pops;
+    h->psi = h->ws + lay.off_psi;
+    h->partials = reinterpret_cast<double *>(h->ws + lay.off_partials);
+    h->out = reinterpret_cast<double *>(h->ws + lay.off_out);
+    h->staging = reinterpret_cast<double *>(h->ws + lay.off_staging);
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->t = 0;
     h->odd = 0;
@@ -332,7 +321,7 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     }
     h->opts.rho_ref = k.d.rho_ref;
     k.flags = reinterpret_cast<unsigned *>(h->ws + lay.off_flags);
-    cudaError_t e = cudaMemsetAsync(h->ws + lay.off_psi, 0, (size_t)lay.psi_elems * lay.s_psi, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->psi, 0, (size_t)lay.psi_elems * lay.s_psi, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.flags, 0, 64, h->stream);
     if (e != cudaSuccess) {
         delete h;
@@ -342,11 +331,20 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     return PLB_OK;
 }
 
-void plb_destroy(plb_t *h) { delete h; }
+void plb_destroy(plb_t *h) {
+    if (h && !h->view) delete h;
+}
 
 long long plb_time(const plb_t *h) { return h ? h->t : -1; }
 
 int plb_init(plb_t *h, const double *rho0, const double *u0) {
+    if (h && h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_init");
+    return plb::init_state(h, rho0, u0);
+}
+
+}  // extern "C"
+
+int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
     if (!h || !rho0) return fail(PLB_EINVAL, "NULL argument");
     const long long n = h->lay.n;
     for (long long s = 0; s < n; ++s)
@@ -373,8 +371,11 @@ int plb_init(plb_t *h, const double *rho0, const double *u0) {
     return PLB_OK;
 }
 
+extern "C" {
+
 int plb_step(plb_t *h, int n) {
     if (!h || n < 0) return fail(PLB_EINVAL, "bad argument");
+    if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
     for (int k = 0; k < n; ++k) {
         h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
@@ -387,6 +388,7 @@ int plb_step(plb_t *h, int n) {
 
 int plb_step_timed(plb_t *h, int n, double ms[2]) {
     if (!h || n < 0 || !ms) return fail(PLB_EINVAL, "bad argument");
+    if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
     ms[0] = ms[1] = 0.0;
     if (n == 0) return PLB_OK;
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
@@ -465,8 +467,8 @@ int plb_reduce(plb_t *h, int what, const int lo[3], const int hi[3], double *out
     if (needs_force) h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
     long long nb = (h->lay.n + 255) / 256;
     const int nblocks = (int)(nb < h->lay.max_blocks ? nb : h->lay.max_blocks);
-    double *partials = reinterpret_cast<double *>(h->ws + h->lay.off_partials);
-    double *dout = reinterpret_cast<double *>(h->ws + h->lay.off_out);
+    double *partials = h->partials;
+    double *dout = h->out;
     h->L->reduce(h->kp, pops_ptr(h), psi_ptr(h), h->odd, what, blo, bhi, partials, nblocks, h->stream);
     int st = check_launch();
     if (st) return st;
@@ -505,6 +507,7 @@ int plb_get_populations(plb_t *h, double *f) {
 
 int plb_set_populations(plb_t *h, const double *f) {
     if (!h || !f) return fail(PLB_EINVAL, "NULL argument");
+    if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: populations are read-only here");
     const long long n = h->lay.n, chunk = h->lay.chunk;
     double *stg = staging_ptr(h);
     for (long long c0 = 0; c0 < n; c0 += chunk) {
@@ -540,6 +543,7 @@ int plb_get_state(plb_t *h, void *host_buf, size_t bytes) {
 
 int plb_set_state(plb_t *h, const void *host_buf, size_t bytes) {
     if (!h || !host_buf) return fail(PLB_EINVAL, "NULL argument");
+    if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: its state is read-only here");
     if (bytes < plb_state_bytes(h)) return fail(PLB_ENOMEM, "state buffer too small");
     long long hdr[8];
     std::memcpy(hdr, host_buf, sizeof(hdr));

@@ -24,11 +24,10 @@ template <class I> struct Geo {
     __device__ __forceinline__ I nb(int cx, int cy, int cz) const { return ox[cx + 1] + oy[cy + 1] + oz[cz + 1]; }
 };
 
-template <class I> __device__ __forceinline__ bool make_geo(const KParams &p, Geo<I> &g) {
-    g.x = blockIdx.x * blockDim.x + threadIdx.x;
-    g.y = blockIdx.y * blockDim.y + threadIdx.y;
-    g.z = blockIdx.z;
-    if (g.x >= p.nx || g.y >= p.ny) return false;
+template <class I> __device__ __forceinline__ void geo_at(const KParams &p, int x, int y, int z, Geo<I> &g) {
+    g.x = x;
+    g.y = y;
+    g.z = z;
     const I row = (I)p.nx, plane = (I)p.nx * (I)p.ny;
     g.s = (I)g.x + row * ((I)g.y + (I)p.ny * (I)g.z);
     g.ox[1] = g.oy[1] = g.oz[1] = 0;
@@ -38,12 +37,18 @@ template <class I> __device__ __forceinline__ bool make_geo(const KParams &p, Ge
     g.oy[2] = g.y < p.ny - 1 ? row : -row * (I)(p.ny - 1);
     g.oz[0] = g.z > 0 ? -plane : plane * (I)(p.nz - 1);
     g.oz[2] = g.z < p.nz - 1 ? plane : -plane * (I)(p.nz - 1);
+}
+
+template <class I> __device__ __forceinline__ bool make_geo(const KParams &p, Geo<I> &g) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= p.nx || y >= p.ny) return false;
+    geo_at<I>(p, x, y, blockIdx.z, g);
     return true;
 }
 
 // Stored values of the pre-collision populations for parity ODD (for FP16 storage the
 // deviations f_i - w_i rho_ref).  WALL: this row touches a bounce-back wall.
-template <class L, class S, bool ODD, bool WALL, class I>
+template <class L, class S, bool ODD, bool WALL, class Pol = LdStream, class I>
 __device__ __forceinline__ void load_fast(const KParams &p, const Planes<S> &A, const Geo<I> &g,
                                           typename Store<S>::T *f) {
     Unroll<0, L::Q>::run([&](auto ic) {
@@ -51,14 +56,14 @@ __device__ __forceinline__ void load_fast(const KParams &p, const Planes<S> &A, 
         constexpr int o = opp(i);
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         if (!ODD) {
-            f[i] = Store<S>::ld(A.p[i] + g.s);
+            f[i] = Store<S>::template ld<Pol>(A.p[i] + g.s);
         } else {
             bool from_wall = false;
             if (WALL && cy != 0) from_wall = (g.y - cy < 0) || (g.y - cy >= p.ny);
             if (from_wall)
-                f[i] = Store<S>::ld(A.p[i] + g.s);
+                f[i] = Store<S>::template ld<Pol>(A.p[i] + g.s);
             else
-                f[i] = Store<S>::ld(A.p[o] + (g.s + g.nb(-cx, -cy, -cz)));
+                f[i] = Store<S>::template ld<Pol>(A.p[o] + (g.s + g.nb(-cx, -cy, -cz)));
         }
     });
 }
@@ -84,9 +89,9 @@ __device__ __forceinline__ void store_fast(const KParams &p, const Planes<S> &A,
 }
 
 // Total force density from the padded psi field (pc points at the cell's psi).
-template <class L, class T, class PsiT>
+template <class L, class T, class Pol = LdStream, class PsiT>
 __device__ __forceinline__ void force_fast(const KParams &p, const PsiT *__restrict__ pc, T F[3]) {
-    const T psi0 = (T)__ldg(pc);
+    const T psi0 = (T)Pol::ro(pc);
     T m1[3] = {0, 0, 0};
     T m2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const int sy = p.px, sz = p.px * p.py;
@@ -94,7 +99,7 @@ __device__ __forceinline__ void force_fast(const KParams &p, const PsiT *__restr
         constexpr int i = 2 * decltype(kc)::value + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const int off = cx + cy * sy + cz * sz;
-        const T pa = (T)__ldg(pc + off), pb = (T)__ldg(pc - off);
+        const T pa = (T)Pol::ro(pc + off), pb = (T)Pol::ro(pc - off);
         const T dif = pa - pb;
         const T sym = (pa + pb) - (T)2 * psi0;
         constexpr double w3 = 3.0 * L::w(i), w9 = 9.0 * L::w(i);
@@ -254,13 +259,13 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
 #define PLB_COLLIDE_MINB 3
 #endif
 
-template <class L, class S, bool ODD, bool WALL, class I>
+template <class L, class S, bool ODD, bool WALL, class Pol = LdStream, class I>
 __device__ __forceinline__ void psi_body(const KParams &p, const Planes<S> &A, typename Store<S>::PsiT *psi,
                                          const Geo<I> &g) {
     using T = typename Store<S>::T;
     using PsiT = typename Store<S>::PsiT;
     T f[L::Q];
-    load_fast<L, S, ODD, WALL>(p, A, g, f);
+    load_fast<L, S, ODD, WALL, Pol>(p, A, g, f);
     T rho = f[0];
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) rho += f[i];
@@ -305,14 +310,14 @@ __global__ void __launch_bounds__(256) k_psi_fast(KParams p, Planes<S> A, typena
         psi_body<L, S, ODD, false>(p, A, psi, g);
 }
 
-template <class L, class S, int MRT, bool ODD, bool WALL, class I>
+template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, class I>
 __device__ __forceinline__ void collide_body(const KParams &p, const Planes<S> &A,
                                              const typename Store<S>::PsiT *__restrict__ psi, const Geo<I> &g) {
     using T = typename Store<S>::T;
     T f[L::Q];
-    load_fast<L, S, ODD, WALL>(p, A, g, f);
+    load_fast<L, S, ODD, WALL, Pol>(p, A, g, f);
     T F[3];
-    force_fast<L, T>(p, psi + psi_index(p, g.x, g.y, g.z), F);
+    force_fast<L, T, Pol>(p, psi + psi_index(p, g.x, g.y, g.z), F);
     collide_fast<L, MRT, Store<S>::SHIFT, T>(p, f, F);
     store_fast<L, S, ODD, WALL>(p, A, g, f);
 }
