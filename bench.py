@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--collision", default="mrt", choices=["mrt", "bgk"])
     ap.add_argument("--dims", default="512x256x256")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="plates", choices=["plates", "batch96"],
+                    help="plates: D3Q19 512x256x256 two-phase plates; batch96: 96 uneven D2Q9 instances")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -366,10 +368,105 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------- batch workload
+
+def batch96_instances(plb, precision, collision):
+    """96 D2Q9 instances: sides in {64, ..., 512}, static / translating droplets and planar
+    interfaces, T/Tc in [0.7, 0.9] (seeded); FP32, tau = 1, eps = 2, kappa = 1."""
+    from paper_2504_15018_gb300 import inputs
+    desc = inputs.batched_d2q9_instances(96)
+    insts, fields = [], []
+    for k, d in enumerate(desc):
+        side = d["side"]
+        eos = plb.pr_eos(d["T_over_Tc"])
+        rv, rl, _ = plb.plb_solve_params(eos)
+        opts = plb.make_opts(precision=PREC[precision], collision=plb.PLB_MRT if collision == "mrt" else plb.PLB_BGK,
+                             **MRT_RATES)
+        insts.append(plb.make_instance((side, side, 1), eos, tau=1.0, opts=opts))
+        dims = (side, side, 1)
+        u0 = None
+        if d["kind"] == "planar":
+            rho = inputs.slab(dims, 1, side // 4, 3 * side // 4, rl, rv, 4.0)
+        else:
+            rho = inputs.droplet(dims, (side / 2, side / 2), d["radius"], rv, rl, 4.0)
+            if d["kind"] == "translating":
+                u0 = np.zeros((2, side * side))
+                u0[0], u0[1] = d["velocity"]
+        fields.append((rho, u0))
+    return insts, fields, desc
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2504_15018_gb300 as plb
+    torch.cuda.set_device(0)
+    prec = args.precision
+    insts, fields, desc = batch96_instances(plb, prec, args.collision)
+    cells = sum(i.dims[0] * i.dims[1] for i in insts)
+    b = plb.Batch(plb.PLB_D2Q9, insts)
+    for k, (rho, u0) in enumerate(fields):
+        b.init(k, rho, u0)
+    tile, bps, _ = b.autotune(3)
+    b.step(max(args.warmup, 3))
+    b.status()
+    st = b.stream
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    b.step(args.steps)
+    e1.record(st)
+    e1.synchronize()
+    clocks = sampler.stop()
+    b.status()
+    t = e0.elapsed_time(e1) / 1e3
+    value = cells * args.steps / t / 1e9
+    bpc = 3 * 9 * POP_BYTES[prec] + 2 * PSI_BYTES[prec]
+    peak, peak_kind = peak_hbm()
+    # the same instances stepped one lattice at a time (two launches per instance and step)
+    lats = []
+    for k, (rho, u0) in enumerate(fields):
+        lat = plb.Lattice(plb.PLB_D2Q9, tuple(insts[k].dims), insts[k].eos, 1.0, -1.0, 2.0, opts=insts[k].opts)
+        lat.init(rho, u0)
+        lats.append(lat)
+    nsep = min(args.steps, 50)
+    for lat in lats:
+        lat.step(2)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(nsep):
+        for lat in lats:
+            lat.step(1)
+    e1.record()
+    e1.synchronize()
+    t_sep = e0.elapsed_time(e1) / 1e3
+    sep_glups = cells * nsep / t_sep / 1e9
+    del lats
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic (seeded)",
+            "config": {"workload": f"d2q9_batch96_uneven_{prec}_{args.collision}", "instances": len(insts),
+                       "cells": cells, "sides": sorted({d['side'] for d in desc}),
+                       "kinds": {k: sum(1 for d in desc if d['kind'] == k) for k in ("static", "translating", "planar")},
+                       "tile_cells": tile, "blocks_per_sm": bps,
+                       "l2": "populations %.2f GB, larger than L2" % (9 * POP_BYTES[prec] * cells / 1e9)},
+            "roofline": {"bound": "hbm", "kernel": "k_batch (persistent, all instances, graph-replayed)",
+                         "achieved": round(value * bpc, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(value * bpc / peak, 4), "traffic": None,
+                         "algorithmic_bytes_per_cell_step": bpc},
+            "clocks": clocks, "gpu_launches": 1,
+            "per_instance_launches": {"glups": round(sep_glups, 4), "launches_per_step": 2 * len(insts)}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch96":
+        run_batch(args)
     else:
         run_gpu(args)
 
