@@ -32,10 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "P-LBM GLUPS and % HBM roofline, FP32/FP16 vs FP64 at matched Laplace error"
-PREC = {"fp64": 0, "fp32": 1, "fp16s": 2}
-POP_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
-PSI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
-DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16 storage / f32 arithmetic"}
+PREC = {"fp64": 0, "fp32": 1, "fp16s": 2, "fp16s_sr": 2}
+POP_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2, "fp16s_sr": 2}
+PSI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4, "fp16s_sr": 4}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16s": "f16 storage / f32 arithmetic",
+         "fp16s_sr": "f16 storage (stochastic rounding) / f32 arithmetic"}
 T_RATIO, BODY_FORCE = 0.8, 1e-7
 MRT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98)
 
@@ -84,7 +85,8 @@ def make_lattice(dims, precision, collision):
     import paper_2504_15018_gb300 as plb
     eos = plb.pr_eos(T_RATIO)
     opts = plb.make_opts(precision=PREC[precision], collision=plb.PLB_MRT if collision == "mrt" else plb.PLB_BGK,
-                         wall_y=1, body_force=(BODY_FORCE, 0.0, 0.0), **MRT_RATES)
+                         wall_y=1, body_force=(BODY_FORCE, 0.0, 0.0), fp16_rounding=int(precision == "fp16s_sr"),
+                         **MRT_RATES)
     return plb.Lattice(plb.PLB_D3Q19, dims, eos, tau=1.0, G=-1.0, eps=2.0, opts=opts)
 
 
@@ -266,7 +268,7 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants:
-        for prec in ("fp16s", "fp64", "fp32"):
+        for prec in ("fp16s", "fp16s_sr", "fp64", "fp32"):
             if prec == args.precision:
                 continue
             lv = make_lattice(dims, prec, args.collision)

@@ -99,6 +99,8 @@ typedef struct plb_opts {
     int wall_y;              /* 1: halfway bounce-back walls at y = -1/2 and y = ny - 1/2;
                                 psi on the wall equals psi of the adjacent fluid row [0 = periodic] */
     double body_force[3];    /* external force density F_ext added to F (Sec. II) [0] */
+    int fp16_rounding;       /* PLB_FP16S stores: 0 round to nearest even; 1 stochastic rounding
+                                (unbiased: no drift from repeated rounding, no stagnation) [0] */
 } plb_opts;
 
 typedef struct plb_state plb_t;

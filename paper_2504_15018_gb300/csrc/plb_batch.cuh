@@ -40,8 +40,8 @@ __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned expected, unsig
     return s_ok != 0;
 }
 
-template <class L, class S, int MRT, bool PSI>
-__device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile &tl, int odd) {
+template <class L, class S, int MRT, bool PSI, bool SR>
+__device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile &tl, int odd, unsigned salt) {
     const KParams &p = in.kp;
     const Planes<S> &A = *reinterpret_cast<const Planes<S> *>(in.pl);
     using PsiT = typename Store<S>::PsiT;
@@ -61,9 +61,9 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
                     else if (wall) psi_pair_body<L, S, true, true, LdCoherent>(p, A, psi, g);
                     else psi_pair_body<L, S, true, false, LdCoherent>(p, A, psi, g);
                 } else {
-                    if (!odd) collide_pair_body<L, S, MRT, false, false, LdCoherent>(p, A, psi, g);
-                    else if (wall) collide_pair_body<L, S, MRT, true, true, LdCoherent>(p, A, psi, g);
-                    else collide_pair_body<L, S, MRT, true, false, LdCoherent>(p, A, psi, g);
+                    if (!odd) collide_pair_body<L, S, MRT, false, false, LdCoherent, SR>(p, A, psi, g, salt);
+                    else if (wall) collide_pair_body<L, S, MRT, true, true, LdCoherent, SR>(p, A, psi, g, salt);
+                    else collide_pair_body<L, S, MRT, true, false, LdCoherent, SR>(p, A, psi, g, salt);
                 }
                 done = true;
             }
@@ -77,9 +77,9 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
                 else if (wall) psi_body<L, S, true, true, LdCoherent>(p, A, psi, g);
                 else psi_body<L, S, true, false, LdCoherent>(p, A, psi, g);
             } else {
-                if (!odd) collide_body<L, S, MRT, false, false, LdCoherent>(p, A, psi, g);
-                else if (wall) collide_body<L, S, MRT, true, true, LdCoherent>(p, A, psi, g);
-                else collide_body<L, S, MRT, true, false, LdCoherent>(p, A, psi, g);
+                if (!odd) collide_body<L, S, MRT, false, false, LdCoherent, SR>(p, A, psi, g, salt);
+                else if (wall) collide_body<L, S, MRT, true, true, LdCoherent, SR>(p, A, psi, g, salt);
+                else collide_body<L, S, MRT, true, false, LdCoherent, SR>(p, A, psi, g, salt);
             }
         }
     }
@@ -87,23 +87,34 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
 
 template <class L, class S, int MRT>
 __global__ void __launch_bounds__(256, 1) k_batch(BatchLaunch b) {
+    const unsigned salt0 = *reinterpret_cast<volatile unsigned *>(&b.bar->salt);
     for (int step = 0; step < b.nsteps; ++step) {
         for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
             const BatchTile tl = b.tiles[t];
             const BatchInst &in = b.insts[tl.inst];
-            batch_tile<L, S, MRT, true>(in, tl, (in.odd + step) & 1);
+            batch_tile<L, S, MRT, true, false>(in, tl, (in.odd + step) & 1, 0);
         }
         if (!grid_sync(b.bar, b.expected, b.spin_limit)) return;
         for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
             const BatchTile tl = b.tiles[t];
             const BatchInst &in = b.insts[tl.inst];
-            batch_tile<L, S, MRT, false>(in, tl, (in.odd + step) & 1);
+            const int odd = (in.odd + step) & 1;
+            if constexpr (Store<S>::SHIFT) {
+                if (in.kp.stochastic) {
+                    batch_tile<L, S, MRT, false, true>(in, tl, odd, salt0 + step);
+                    continue;
+                }
+            }
+            batch_tile<L, S, MRT, false, false>(in, tl, odd, 0);
         }
         if (!grid_sync(b.bar, b.expected, b.spin_limit)) return;
     }
-    // every block has passed the last barrier: advance the stored parities
-    if (blockIdx.x == 0 && (b.nsteps & 1))
-        for (int k = threadIdx.x; k < b.ninst; k += blockDim.x) b.insts[k].odd ^= 1;
+    // every block has passed the last barrier: advance the stored parities and the step salt
+    if (blockIdx.x == 0) {
+        if (b.nsteps & 1)
+            for (int k = threadIdx.x; k < b.ninst; k += blockDim.x) b.insts[k].odd ^= 1;
+        if (threadIdx.x == 0) b.bar->salt = salt0 + b.nsteps;
+    }
 }
 
 }  // namespace plb

@@ -56,6 +56,24 @@ struct D3Q19 {
     __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
 };
 
+// Weights used by the collision in a reduced-precision type R.  The FP32 roundings of 1/36,
+// 1/18 (or 1/9) and 1/3 (or 4/9) sum to 1 + 2^-27 (D2Q9) or 1 + 2^-26 (D3Q19); a relaxation
+// toward an equilibrium whose weights do not sum to one changes the cell's mass by that
+// fraction, the same sign every step, so FP32 lattices gained about 1e-8 of their mass per step.
+// Here w(|c|^2 = 2) is 1/36 rounded to an FP32 value with an even significand, the |c|^2 = 1
+// weight is a power-of-two multiple of it, and the rest weight is one minus the others; all
+// three are exact FP32 values (the even significand makes the difference representable) and
+// they sum to exactly one.  FP64 keeps the plain weights.
+template <class L, class R>
+__host__ __device__ constexpr double wcol(int i) {
+    if (sizeof(R) == sizeof(double)) return L::w(i);
+    constexpr double w2 = 0x1.c71c70p-6;                       // 1/36 (1 - 2.1e-7)
+    constexpr double r1 = L::Q == 9 ? 4.0 : 2.0;               // w(|c|=1) / w(|c|^2=2)
+    constexpr int n1 = L::Q == 9 ? 4 : 6, n2 = L::Q == 9 ? 4 : 12;
+    const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
+    return c2 == 0 ? 1.0 - n1 * r1 * w2 - n2 * w2 : (c2 == 1 ? r1 * w2 : w2);
+}
+
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
 // ------------------------------------------------------------ MRT moment bases
@@ -148,7 +166,33 @@ template <> struct Store<__half> {
     __device__ static void st(__half *a, T v) {
         __stcs(reinterpret_cast<unsigned short *>(a), __half_as_ushort(__float2half_rn(v)));
     }
+    // Stochastic rounding: uniform noise of +-1/2 FP16 ulp (at v's magnitude) added before
+    // round-to-nearest, so the stored value is v in expectation.  r: 16 random bits.
+    __device__ static float sr_dither(float v, unsigned r) {
+        int e = (int)(__float_as_uint(v) & 0x7f800000u) - (10 << 23);    // 2^(exp - 10)
+        e = e > ((127 - 24) << 23) ? e : ((127 - 24) << 23);            // subnormal halves: 2^-24
+        const float ulp = __uint_as_float((unsigned)e);
+        const float u = __uint_as_float(0x3f800000u | ((r & 0xffffu) << 7)) - 1.5f;   // [-1/2, 1/2)
+        return fmaf(ulp, u, v);
+    }
+    __device__ static void st_sr(__half *a, T v, unsigned r) { st(a, sr_dither(v, r)); }
 };
+
+// Counter-based random bits for stochastic rounding: a 32-bit finaliser (murmur3 fmix32)
+// of the cell index and the step counter, then one multiply-xorshift per direction.
+__device__ __forceinline__ unsigned cell_hash(unsigned s, unsigned salt) {
+    unsigned h = s * 0x9e3779b1u ^ (salt + 0x7f4a7c15u) * 0x85ebca6bu;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned dir_bits(unsigned h, int i) {
+    unsigned r = (h ^ (0x9e3779b9u * (unsigned)(i + 1))) * 0xc2b2ae35u;
+    return r ^ (r >> 15);
+}
 
 // Parameters in the arithmetic precision.
 template <class T> __device__ __forceinline__ const Phys<T> &phys(const KParams &p);

@@ -33,6 +33,8 @@ struct KParams {
     long long psi_origin; // element offset of interior cell (0, 0, 0)
     int var_tau;
     int eos_kind;         // 0 PR, 1 paper
+    int stochastic;       // FP16 stores with stochastic rounding
+    unsigned salt;        // step counter mixed into the rounding noise
     Phys<double> d;
     Phys<float> f;
     unsigned *flags;
@@ -54,7 +56,7 @@ struct BatchTile {
 };
 // Grid barrier state (device memory, zeroed at creation).
 struct GridBar {
-    unsigned count, gen, err, pad;
+    unsigned count, gen, err, salt;   // salt: steps taken, for the stochastic rounding noise
 };
 // Launch parameters of the persistent kernel.
 struct BatchLaunch {

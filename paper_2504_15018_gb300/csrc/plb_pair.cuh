@@ -45,6 +45,10 @@ template <> struct PairIO<__half> {
         Store<__half>::st(a0, v.v.x);
         Store<__half>::st(a1, v.v.y);
     }
+    // stochastic rounding, 16 random bits per cell from r
+    __device__ static f2 dither(f2 v, unsigned r) {
+        return f2(Store<__half>::sr_dither(v.v.x, r), Store<__half>::sr_dither(v.v.y, r >> 16));
+    }
 };
 
 // Geometry of the cell pair: shared row offsets, per-cell x offsets with the wrap.
@@ -106,25 +110,30 @@ __device__ __forceinline__ void load_pair(const KParams &p, const Planes<S> &A, 
     });
 }
 
-template <class L, class S, bool ODD, bool WALL>
-__device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, const f2 *f) {
+template <class L, class S, bool ODD, bool WALL, bool SR = false>
+__device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, const f2 *f,
+                                           unsigned salt = 0) {
+    unsigned hsh = 0;
+    if constexpr (SR) hsh = cell_hash((unsigned)g.s0, salt);
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int o = opp(i);
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        f2 v = f[i];
+        if constexpr (SR) v = PairIO<S>::dither(v, dir_bits(hsh, i));
         if (!ODD) {
-            PairIO<S>::st2(A.p[o] + g.s0, f[i]);
+            PairIO<S>::st2(A.p[o] + g.s0, v);
         } else {
             bool to_wall = false;
             if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
             if (to_wall) {
-                PairIO<S>::st2(A.p[o] + g.s0, f[i]);
+                PairIO<S>::st2(A.p[o] + g.s0, v);
             } else {
                 const int r = g.s0 + g.oy[1 + cy] + g.oz[1 + cz];
                 if (cx == 0)
-                    PairIO<S>::st2(A.p[i] + r, f[i]);
+                    PairIO<S>::st2(A.p[i] + r, v);
                 else
-                    PairIO<S>::st11(A.p[i] + (r + g.ox0[1 + cx]), A.p[i] + (r + 1 + g.ox1[1 + cx]), f[i]);
+                    PairIO<S>::st11(A.p[i] + (r + g.ox0[1 + cx]), A.p[i] + (r + 1 + g.ox1[1 + cx]), v);
             }
         }
     });
@@ -270,15 +279,15 @@ __global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float 
 #define PLB_PAIR_MINB 2
 #endif
 
-template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream>
+template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, bool SR = false>
 __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes<S> &A, const float *__restrict__ psi,
-                                                  const GeoPair &g) {
+                                                  const GeoPair &g, unsigned salt = 0) {
     f2 f[L::Q];
     load_pair<L, S, ODD, WALL, Pol>(p, A, g, f);
     f2 F[3];
     force_pair<L, Pol>(p, psi + psi_index(p, g.x0, g.y, g.z), F);
     collide_fast<L, MRT, Store<S>::SHIFT, f2>(p, f, F);
-    store_pair<L, S, ODD, WALL>(p, A, g, f);
+    store_pair<L, S, ODD, WALL, SR>(p, A, g, f, salt);
 }
 
 template <class L, class S, int MRT, bool ODD>
@@ -286,7 +295,15 @@ __global__ void __launch_bounds__(256, PLB_PAIR_MINB) k_collide_pair(KParams p, 
                                                                     const float *__restrict__ psi) {
     GeoPair g;
     if (!make_geo_pair(p, g)) return;
-    if (ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1))
+    const bool wall = ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1);
+    if constexpr (Store<S>::SHIFT) {
+        if (p.stochastic) {
+            if (wall) collide_pair_body<L, S, MRT, ODD, true, LdStream, true>(p, A, psi, g, p.salt);
+            else collide_pair_body<L, S, MRT, ODD, false, LdStream, true>(p, A, psi, g, p.salt);
+            return;
+        }
+    }
+    if (wall)
         collide_pair_body<L, S, MRT, ODD, true>(p, A, psi, g);
     else
         collide_pair_body<L, S, MRT, ODD, false>(p, A, psi, g);

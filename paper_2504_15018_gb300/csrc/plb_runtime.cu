@@ -194,6 +194,7 @@ int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos,
     if (!std::isfinite(eps) || !std::isfinite(o.kappa)) return fail(PLB_EINVAL, "eps and kappa must be finite");
     if (o.collision != PLB_BGK && o.collision != PLB_MRT) return fail(PLB_EINVAL, "bad collision");
     if (o.tau_v > 0.0 && !(o.tau_v > 0.5)) return fail(PLB_EINVAL, "tau_v must be > 1/2");
+    if (o.fp16_rounding != 0 && o.fp16_rounding != 1) return fail(PLB_EINVAL, "fp16_rounding must be 0 or 1");
     if (eos->kind == PLB_EOS_PR) {
         if (!(eos->a > 0 && eos->b > 0 && eos->R > 0 && eos->T_over_Tc > 0)) return fail(PLB_EINVAL, "bad PR constants");
     } else if (eos->kind == PLB_EOS_PAPER) {
@@ -258,6 +259,8 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
         d.pe_sv = std::sqrt(eos.rho_v);
     }
     d.p_scale = eos.p_scale;
+    k.stochastic = o.precision == PLB_FP16S && o.fp16_rounding == 1;
+    k.salt = 0;
     // FP32 copy (rounded once here, not per thread)
     Phys<float> &f = k.f;
     const double *src = reinterpret_cast<const double *>(&d);
@@ -378,6 +381,7 @@ int plb_step(plb_t *h, int n) {
     if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
     for (int k = 0; k < n; ++k) {
+        h->kp.salt = (unsigned)h->t;
         h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
         h->L->collide[coll](h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
         h->odd ^= 1;
@@ -397,6 +401,7 @@ int plb_step_timed(plb_t *h, int n, double ms[2]) {
     int st = PLB_OK;
     PLB_CUDA(cudaEventRecord(ev[0], h->stream));
     for (int k = 0; k < n; ++k) {
+        h->kp.salt = (unsigned)h->t;
         h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
         cudaEventRecord(ev[2 * k + 1], h->stream);
         h->L->collide[coll](h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);

@@ -68,22 +68,29 @@ __device__ __forceinline__ void load_fast(const KParams &p, const Planes<S> &A, 
     });
 }
 
-template <class L, class S, bool ODD, bool WALL, class I>
+// SR: FP16 stores with stochastic rounding, random bits from cell_hash(cell, salt).
+template <class L, class S, bool ODD, bool WALL, bool SR = false, class I>
 __device__ __forceinline__ void store_fast(const KParams &p, const Planes<S> &A, const Geo<I> &g,
-                                           const typename Store<S>::T *f) {
+                                           const typename Store<S>::T *f, unsigned salt = 0) {
+    unsigned hsh = 0;
+    if constexpr (SR) hsh = cell_hash((unsigned)g.s, salt);
+    auto st = [&](S *a, typename Store<S>::T v, int i) {
+        if constexpr (SR) Store<S>::st_sr(a, v, dir_bits(hsh, i));
+        else Store<S>::st(a, v);
+    };
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         constexpr int o = opp(i);
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         if (!ODD) {
-            Store<S>::st(A.p[o] + g.s, f[i]);
+            st(A.p[o] + g.s, f[i], i);
         } else {
             bool to_wall = false;
             if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
             if (to_wall)
-                Store<S>::st(A.p[o] + g.s, f[i]);
+                st(A.p[o] + g.s, f[i], i);
             else
-                Store<S>::st(A.p[i] + (g.s + g.nb(cx, cy, cz)), f[i]);
+                st(A.p[i] + (g.s + g.nb(cx, cy, cz)), f[i], i);
         }
     });
 }
@@ -163,7 +170,8 @@ template <int CX, int CY, int CZ, class T> __device__ __forceinline__ T dot_c(co
 
 // In place: stored values h -> post-collision stored values.  SHIFT: h_i = f_i - w_i rho_ref
 // (FP16 storage); then rho = sum h + rho_ref (sum_i w_i = 1), j = sum c_i h_i
-// (sum_i w_i c_i = 0), f_i - feq_i = h_i - w_i (rho t2 - rho_ref), and the update adds to h.
+// (sum_i w_i c_i = 0), f_i - feq_i = h_i - w_i (rho - rho_ref) - w_i rho delta_i, and the
+// update adds to h.
 // T is double, float, or f2 (two cells at once).
 template <class L, int MRT, bool SHIFT, class T>
 __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3]) {
@@ -183,15 +191,18 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
     const T u[3] = {mad(T(0.5), F[0], j[0]) * irho, mad(T(0.5), F[1], j[1]) * irho, mad(T(0.5), F[2], j[2]) * irho};
     const T om = omega_of<T>(p, rho);
     const T nom = -om;
-    const T Aeq = mad(T(-1.5), mad(u[0], u[0], mad(u[1], u[1], u[2] * u[2])), T(1));
+    // feq_i = w_i rho (1 + delta_i), delta_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2, kept without the 1 so
+    // that the u^2 terms are not lost to rounding against 1 (sum_i w_i delta_i = 0 exactly in
+    // exact arithmetic; rounding the 1 + ... away biases the mass at small u).
+    const T Bq = T(-1.5) * mad(u[0], u[0], mad(u[1], u[1], u[2] * u[2]));
     const T nuF3 = T(-3) * mad(u[0], F[0], mad(u[1], F[1], u[2] * F[2]));
     const T kguo = mad(T(-0.5), om, T(1));
-    const T nrref = T(-q.rho_ref);
+    const T drho = SHIFT ? rho - T(q.rho_ref) : rho;     // rho minus the stored shift
     T g[L::Q];
-    // one direction: t2 = feq / (w rho), t4 = Ft / w
-    auto update = [&](int i, double w, const T &t2, const T &t4) {
-        const T dn = SHIFT ? mad(T(-w), mad(rho, t2, nrref), f[i])    // f - feq
-                           : mad(T(-w) * rho, t2, f[i]);
+    // one direction: delta = feq / (w rho) - 1, t4 = Ft / w
+    auto update = [&](int i, double w, const T &delta, const T &t4) {
+        const T wrho = T(w) * rho;
+        const T dn = mad(-wrho, delta, f[i] - T(w) * drho);          // f - feq
         if (!MRT) {
             f[i] = mad(kguo * T(w), t4, mad(nom, dn, f[i]));
         } else {
@@ -199,16 +210,16 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
             f[i] = mad(nom, g[i], mad(T(w), t4, f[i]));           // BGK part with Ft
         }
     };
-    update(0, L::w(0), Aeq, nuF3);
+    update(0, wcol<L, R>(0), Bq, nuF3);
     // opposite pair (i, i + 1): c_{i+1} = -c_i, the first non-zero component of c_i is +1
     Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
         constexpr int i = 2 * decltype(kc)::value + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const T cu = dot_c<cx, cy, cz>(u);
         const T cF = dot_c<cx, cy, cz>(F);
-        constexpr double w = L::w(i);
-        update(i, w, mad(cu, mad(T(4.5), cu, T(3)), Aeq), mad(cF, mad(T(9), cu, T(3)), nuF3));
-        update(i + 1, w, mad(cu, mad(T(4.5), cu, T(-3)), Aeq), mad(cF, mad(T(9), cu, T(-3)), nuF3));
+        constexpr double w = wcol<L, R>(i);
+        update(i, w, mad(cu, mad(T(4.5), cu, T(3)), Bq), mad(cF, mad(T(9), cu, T(3)), nuF3));
+        update(i + 1, w, mad(cu, mad(T(4.5), cu, T(-3)), Bq), mad(cF, mad(T(9), cu, T(-3)), nuF3));
     });
     if (MRT) {
         constexpr int NP = (L::Q - 1) / 2;
@@ -310,16 +321,17 @@ __global__ void __launch_bounds__(256) k_psi_fast(KParams p, Planes<S> A, typena
         psi_body<L, S, ODD, false>(p, A, psi, g);
 }
 
-template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, class I>
+template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, bool SR = false, class I>
 __device__ __forceinline__ void collide_body(const KParams &p, const Planes<S> &A,
-                                             const typename Store<S>::PsiT *__restrict__ psi, const Geo<I> &g) {
+                                             const typename Store<S>::PsiT *__restrict__ psi, const Geo<I> &g,
+                                             unsigned salt = 0) {
     using T = typename Store<S>::T;
     T f[L::Q];
     load_fast<L, S, ODD, WALL, Pol>(p, A, g, f);
     T F[3];
     force_fast<L, T, Pol>(p, psi + psi_index(p, g.x, g.y, g.z), F);
     collide_fast<L, MRT, Store<S>::SHIFT, T>(p, f, F);
-    store_fast<L, S, ODD, WALL>(p, A, g, f);
+    store_fast<L, S, ODD, WALL, SR>(p, A, g, f, salt);
 }
 
 template <class L, class S, int MRT, bool ODD, class I>
@@ -327,7 +339,15 @@ __global__ void __launch_bounds__(256, PLB_COLLIDE_MINB) k_collide_fast(KParams 
                                                       const typename Store<S>::PsiT *__restrict__ psi) {
     Geo<I> g;
     if (!make_geo<I>(p, g)) return;
-    if (ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1))
+    const bool wall = ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1);
+    if constexpr (Store<S>::SHIFT) {
+        if (p.stochastic) {
+            if (wall) collide_body<L, S, MRT, ODD, true, LdStream, true>(p, A, psi, g, p.salt);
+            else collide_body<L, S, MRT, ODD, false, LdStream, true>(p, A, psi, g, p.salt);
+            return;
+        }
+    }
+    if (wall)
         collide_body<L, S, MRT, ODD, true>(p, A, psi, g);
     else
         collide_body<L, S, MRT, ODD, false>(p, A, psi, g);
