@@ -65,6 +65,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(seconds: float, world: int, device) -> float:
+    """The job time of a multi-rank run: the slowest rank's time (all_reduce MAX)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_glups(cells_per_rank: int, steps: int, seconds: float, world: int) -> float:
+    """Whole-job lattice updates per second (1e9): every rank advances its own replica of
+    cells_per_rank cells by steps steps (weak scaling), timed by the slowest rank."""
+    return world * cells_per_rank * steps / seconds / 1e9
+
+
 def workload_name(dims, precision, collision):
     return f"d3q19_plates_{dims[0]}x{dims[1]}x{dims[2]}_{precision}_{collision}_pr0.8"
 
@@ -213,11 +230,8 @@ def run_gpu(args):
     barrier()
     clocks = sampler.stop()
     lat.status()
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * ncell * args.steps / t / 1e9
+    t = max_over_ranks(t, world, "cuda")
+    value = job_glups(ncell, args.steps, t, world)
 
     # roofline of the dominant kernel (fused pass), per-launch events on the same stream
     nprof = min(args.steps, 20)
@@ -253,13 +267,10 @@ def run_gpu(args):
         plb.plb_moments(lat.h, out_rho, out_u, out_p)
         barrier()
         te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(te, world, "cuda")
         h2d = rho_pin.numel() * 8
         d2h = (out_rho.numel() + out_u.numel() + out_p.numel()) * 8 + 8
-        e2e = {"value": round(world * ncell * args.steps / te / 1e9, 4), "unit": "GLUPS",
+        e2e = {"value": round(job_glups(ncell, args.steps, te, world), 4), "unit": "GLUPS",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "what": "plb_init from pinned host rho0 + K steps + plb_reduce(mass) + plb_moments to pinned host",
                "mass": mass}

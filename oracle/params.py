@@ -16,6 +16,8 @@ Contents:
   - the SI unit converter, Eqs. unit and unit2 (Sec. V);
   - the analytic planar profile of App. A and the analytic gamma of App. B;
   - the sharp-interface layered Poiseuille profile used for the plates test
+  - the diffuse-interface channel flow (viscosity varying with the App. A density profile)
+    and the linear relaxation-time interpolation of Sec. VI
     (the paper does not print its analytic solution; this is the textbook one).
 """
 from __future__ import annotations
@@ -287,3 +289,42 @@ def layered_poiseuille(y, layers, F: float):
         m = (y >= lo) & (y <= hi)
         u[m] = -F * y[m] ** 2 / (2 * mu) + coef[2 * k] * y[m] + coef[2 * k + 1]
     return u
+
+
+# --------------------------------------------------------- diffuse-interface channel flow
+
+
+def tau_of_rho(rho, tau_v: float, tau_l: float, rho_v: float, rho_l: float):
+    """Sec. VI: tau = tau_v + (rho - rho_v) / (rho_l - rho_v) (tau_l - tau_v), the weight clamped to
+    [0, 1] outside [rho_v, rho_l]."""
+    wgt = np.clip((np.asarray(rho, dtype=np.float64) - rho_v) / (rho_l - rho_v), 0.0, 1.0)
+    return tau_v + wgt * (tau_l - tau_v)
+
+
+def channel_flow(y, mu, F: float, y_lo: float, y_hi: float, breaks=()):
+    """Steady u_x(y) of a body-force-driven flow between no-slip walls at y_lo and y_hi when the
+    dynamic viscosity varies across the channel (mu: callable of y).
+
+    The x-momentum balance d/dy (mu du/dy) = -F integrates to mu u' = -F (y - y_s), with y_s the
+    height of zero shear; u(y_lo) = 0 gives u(y) = -F int_{y_lo}^{y} (s - y_s) / mu(s) ds and
+    u(y_hi) = 0 fixes y_s = int s / mu / int 1 / mu over the channel.  For a piecewise constant
+    mu this is the layered Poiseuille solution; for constant mu, the Poiseuille parabola.
+    breaks: heights where mu changes fast (the interfaces), passed to the quadrature."""
+    pts = sorted(b for b in breaks if y_lo < b < y_hi)
+
+    def q(fn, a, b):
+        inner = [p for p in pts if a < p < b]
+        val, _ = integrate.quad(fn, a, b, points=inner or None, epsabs=0.0, epsrel=1e-12, limit=400)
+        return val
+
+    inv = q(lambda s: 1.0 / mu(s), y_lo, y_hi)
+    ys = q(lambda s: s / mu(s), y_lo, y_hi) / inv
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    order = np.argsort(y)
+    out = np.empty_like(y)
+    acc, prev = 0.0, y_lo
+    for j in order:
+        acc += q(lambda s: (s - ys) / mu(s), prev, y[j])
+        prev = y[j]
+        out[j] = -F * acc
+    return out

@@ -156,3 +156,28 @@ def test_layered_poiseuille():
           - pp.layered_poiseuille([5.5 - h], layers, 1e-5)[0]) / h
     dr = (pp.layered_poiseuille([5.5 + h], layers, 1e-5)[0] - pp.layered_poiseuille([5.5], layers, 1e-5)[0]) / h
     assert 3.0 * dl == pytest.approx(0.2 * dr, rel=1e-3)
+
+
+def test_channel_flow_with_constant_viscosity_is_the_poiseuille_parabola():
+    y = np.linspace(-0.5, 31.5, 65)
+    u = pp.channel_flow(y, lambda s: 0.7, 3e-6, -0.5, 31.5)
+    assert np.allclose(u, 3e-6 / (2 * 0.7) * (y + 0.5) * (31.5 - y), rtol=1e-10, atol=1e-15)
+
+
+def test_channel_flow_tends_to_the_layered_solution_as_the_interface_sharpens():
+    """mu(y) = tanh blend of 3.0 (below 10.5) and 0.2 (above) over a width W: the profile
+    approaches the two-layer closed form, with an error that falls in proportion to W."""
+    ys = np.linspace(-0.5, 31.5, 33)
+    sharp = pp.layered_poiseuille(ys, [(-0.5, 10.5, 3.0), (10.5, 31.5, 0.2)], 1e-5)
+    errs = []
+    for W in (0.25, 0.125, 0.0625):
+        mu = lambda s, W=W: 0.2 + 2.8 * 0.5 * (1 - math.tanh((s - 10.5) / W))
+        u = pp.channel_flow(ys, mu, 1e-5, -0.5, 31.5, breaks=(10.5,))
+        errs.append(np.max(np.abs(u - sharp)) / np.max(sharp))
+    assert errs[2] < 0.015
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2
+
+
+def test_tau_interpolation_hits_both_phases_and_clamps():
+    t = pp.tau_of_rho(np.array([0.1, 4.0, 0.05, 9.0, 2.05]), 0.62, 0.56, 0.1, 4.0)
+    assert np.allclose(t, [0.62, 0.56, 0.62, 0.56, 0.59])

@@ -349,3 +349,61 @@ def test_planar_profile_converges_second_order_to_appendix_a():
         errs.append(np.sqrt(((r - rho) ** 2).sum() / (rho ** 2).sum()))
     orders = [math.log(errs[0] / errs[1]) / math.log(2), math.log(errs[1] / errs[2]) / math.log(1.5)]
     assert min(orders) > 1.9, (errs, orders)
+
+
+def _plates_oracle(ny, steps_factor):
+    from paper_setups import plates
+    s = plates(ny)
+    P = oracle.make_params(0, (1, ny, 1), wall_y=True, eos=dict(kind="paper", rho_v=s["rho_v"], rho_l=s["rho_l"],
+                                                                 P=s["P"]),
+                           tau=s["tau_l"], kappa=s["kappa"], tau_v=s["tau_v"], tau_rho=(s["rho_v"], s["rho_l"]),
+                           fext=(s["F"], 0, 0))
+    u0 = np.zeros((2, ny))
+    u0[0] = s["u"]
+    from paper_setups import balanced_init_oracle
+    f = oracle.run(P, balanced_init_oracle(P, 0, s["rho"], u0), int(steps_factor * (ny / 2) ** 2 / s["nu_l"]))
+    _, u, _ = oracle.moments(P, f)
+    from paper_setups import relative_norms
+    return relative_norms(u[0], s["u"])
+
+
+def test_two_phase_channel_converges_to_the_diffuse_interface_profile():
+    """Sec. VI.D (liquid below, vapour above, R134a, tau_l = 0.56, xi = 1.5 cells per 100): the
+    steady velocity converges at second order to the channel flow whose viscosity follows the
+    App. A density profile and the tau(rho) interpolation; the sharp two-layer solution is 14 %
+    away at every resolution, since xi is fixed in physical units.  Started from the diffuse
+    solution, run for half a liquid-layer viscous time (the error is steady by then)."""
+    n64 = _plates_oracle(64, 0.5)
+    n128 = _plates_oracle(128, 0.5)
+    orders = [math.log2(a / b) for a, b in zip(n64, n128)]
+    assert n128[1] < 0.06
+    assert min(orders) > 1.7, (n64, n128, orders)
+
+
+def _galilean_oracle(k):
+    from paper_setups import planar, galilean_steps, relative_norms, balanced_init_oracle, equilibrium
+    s = planar(100 * k)
+    n1, n2, U = galilean_steps(k)
+    nx = 100 * k
+    P = oracle.make_params(0, (nx, 1, 1), eos=dict(kind="paper", rho_v=s["rho_v"], rho_l=s["rho_l"], P=s["P"]),
+                           tau=0.56, kappa=s["kappa"], tau_v=s["tau_v"], tau_rho=(s["rho_v"], s["rho_l"]))
+    f = oracle.run(P, balanced_init_oracle(P, 0, s["rho"]), n1)
+    rho, u, _ = oracle.moments(P, f)
+    c, w = oracle.velocity_set(0)
+    c = c[:, :2].astype(float)
+    u2 = u.copy()
+    u2[0] += U
+    f = np.ascontiguousarray((f.T - equilibrium(c, w, rho, u) + equilibrium(c, w, rho, u2)).T)
+    _, u, _ = oracle.moments(P, oracle.run(P, f, n2))
+    return relative_norms(u[0], np.full(nx, U))
+
+
+def test_galilean_invariance_error_falls_at_second_order():
+    """Sec. VI.C on grids 1 and 2 of Table II: the planar interface, started at rest, is set in
+    uniform motion at U_x = 0.1 m/s at 7.91 us (its equilibrium part shifted by U, the effect of
+    a one-step force rho U); at 31.6 us the error of u_x against U_x falls at second order in
+    all three norms of Eq. relative_norms."""
+    n1, n2 = _galilean_oracle(1), _galilean_oracle(2)
+    orders = [math.log2(a / b) for a, b in zip(n1, n2)]
+    assert min(orders) > 1.8, (n1, n2, orders)
+    assert n1[1] < 0.06
