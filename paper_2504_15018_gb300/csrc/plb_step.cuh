@@ -168,100 +168,191 @@ template <int CX, int CY, int CZ, class T> __device__ __forceinline__ T dot_c(co
     return r;
 }
 
+// MRT ghost-moment part of the collision, generic over the lattice: m_k = sum_i M_ki g_i for
+// the non-hydrodynamic rows, A_k = (s_k - omega) m_k / |M_k|^2, f_i -= sum_k M_ki A_k.
+// g0 = g_0; gs[r] / ga[r] = g_i +- g_{i+1} of the opposite pair r (i = 2 r + 1); the pair's
+// populations are held as fs[r] / fa[r] = f_i +- f_{i+1}, so f_i -= E + O, f_{i+1} -= E - O
+// becomes fs -= 2 E, fa -= 2 O.
+template <class L, class T, class R>
+__device__ __forceinline__ void ghosts_generic(const Phys<R> &q, const T &om, const T &g0, const T *gs,
+                                               const T *ga, T &f0, T *fs, T *fa) {
+    constexpr int NP = (L::Q - 1) / 2;
+    T Ak[Ghosts<L>::K];
+    Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr bool ev = RowParity<L>::even(k);
+        T m = ev ? T(Ghosts<L>::row(k, 0)) * g0 : T(0);
+        Unroll<0, NP>::run([&](auto qc) {
+            constexpr int r = decltype(qc)::value;
+            constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
+            if (c != 0.0) m = mad(T(c), ev ? gs[r] : ga[r], m);
+        });
+        Ak[k] = (T(q.s_rate[Ghosts<L>::kind(k)]) - om) * (T(1.0 / row_norm2<L>(k)) * m);
+    });
+    T e0 = T(0);
+    Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if (RowParity<L>::even(k) && Ghosts<L>::row(k, 0) != 0.0) e0 = mad(T(Ghosts<L>::row(k, 0)), Ak[k], e0);
+    });
+    f0 -= e0;
+    Unroll<0, NP>::run([&](auto qc) {
+        constexpr int r = decltype(qc)::value;
+        T E = T(0), O = T(0);
+        Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
+            if (c != 0.0) {
+                if (RowParity<L>::even(k)) E = mad(T(c), Ak[k], E);
+                else O = mad(T(c), Ak[k], O);
+            }
+        });
+        fs[r] = mad(T(-2), E, fs[r]);
+        fa[r] = mad(T(-2), O, fa[r]);
+    });
+}
+
+// The same for D3Q19 with the rows of the d'Humieres et al. (2002) basis grouped by velocity
+// class: the energy rows see only |c|^2, the pi rows only the axis or plane of c, and every
+// plane's two pairs share their q / m coefficients up to signs, so sums over classes are
+// formed once (pairs: 0-2 axes x, y, z; 3, 4: (1, +-1, 0); 5, 6: (1, 0, +-1); 7, 8: (0, 1, +-1)).
+template <class T, class R>
+__device__ __forceinline__ void ghosts_d3q19(const Phys<R> &q, const T &om, const T &g0, const T *gs,
+                                             const T *ga, T &f0, T *fs, T *fa) {
+    using G = Ghosts<D3Q19>;
+    static_assert(D3Q19::cx(1) == 1 && D3Q19::cy(3) == 1 && D3Q19::cz(5) == 1 &&
+                  D3Q19::cx(7) == 1 && D3Q19::cy(7) == 1 && D3Q19::cx(9) == 1 && D3Q19::cy(9) == -1 &&
+                  D3Q19::cx(11) == 1 && D3Q19::cz(11) == 1 && D3Q19::cx(13) == 1 && D3Q19::cz(13) == -1 &&
+                  D3Q19::cy(15) == 1 && D3Q19::cz(15) == 1 && D3Q19::cy(17) == 1 && D3Q19::cz(17) == -1,
+                  "pair order assumed by the grouped projection");
+    // even rows from the symmetric sums
+    const T sx = gs[0], sy = gs[1], sz = gs[2];
+    const T Dxy = gs[3] + gs[4], Dxz = gs[5] + gs[6], Dyz = gs[7] + gs[8];
+    const T syz = sy + sz;
+    const T S1 = sx + syz, S2 = Dxy + Dxz + Dyz;
+    const T m_e = mad(T(-30), g0, mad(T(-11), S1, T(8) * S2));
+    const T m_eps = mad(T(12), g0, mad(T(-4), S1, S2));
+    const T m_pxx = mad(T(-4), sx, mad(T(2), syz, mad(T(-2), Dyz, Dxy + Dxz)));
+    const T m_pww = mad(T(2), sz - sy, Dxy - Dxz);
+    // odd rows from the antisymmetric sums
+    const T Pxy = ga[3] + ga[4], Qxy = ga[3] - ga[4];
+    const T Pxz = ga[5] + ga[6], Qxz = ga[5] - ga[6];
+    const T Pyz = ga[7] + ga[8], Qyz = ga[7] - ga[8];
+    const T m_qx = mad(T(-4), ga[0], Pxy + Pxz), m_mx = Pxy - Pxz;
+    const T m_qy = mad(T(-4), ga[1], Qxy + Pyz), m_my = Pyz - Qxy;
+    const T m_qz = mad(T(-4), ga[2], Qxz + Qyz), m_mz = Qxz - Qyz;
+    auto A = [&](int k, const T &m) { return (T(q.s_rate[G::kind(k)]) - om) * (T(1.0 / row_norm2<D3Q19>(k)) * m); };
+    const T Ae = A(0, m_e), Aeps = A(1, m_eps), Aqx = A(2, m_qx), Aqy = A(3, m_qy), Aqz = A(4, m_qz);
+    const T Apxx = A(5, m_pxx), Apww = A(6, m_pww), Amx = A(7, m_mx), Amy = A(8, m_my), Amz = A(9, m_mz);
+    // back-projection: f_i -= sum_k M_ki A_k, by class
+    f0 -= mad(T(-30), Ae, T(12) * Aeps);
+    const T C1 = mad(T(-11), Ae, T(-4) * Aeps), C2 = mad(T(8), Ae, Aeps);
+    auto pair = [&](int r, const T &E, const T &O) {
+        fs[r] = mad(T(-2), E, fs[r]);
+        fa[r] = mad(T(-2), O, fa[r]);
+    };
+    pair(0, mad(T(-4), Apxx, C1), T(-4) * Aqx);
+    const T Cy = mad(T(2), Apxx, C1);
+    pair(1, mad(T(-2), Apww, Cy), T(-4) * Aqy);
+    pair(2, mad(T(2), Apww, Cy), T(-4) * Aqz);
+    {
+        const T E = C2 + Apxx + Apww, a = Aqx + Amx, b = Aqy - Amy;
+        pair(3, E, a + b);
+        pair(4, E, a - b);
+    }
+    {
+        const T E = C2 + Apxx - Apww, a = Aqx - Amx, b = Aqz + Amz;
+        pair(5, E, a + b);
+        pair(6, E, a - b);
+    }
+    {
+        const T E = mad(T(-2), Apxx, C2), a = Aqy + Amy, b = Aqz - Amz;
+        pair(7, E, a + b);
+        pair(8, E, a - b);
+    }
+}
+
 // In place: stored values h -> post-collision stored values.  SHIFT: h_i = f_i - w_i rho_ref
 // (FP16 storage); then rho = sum h + rho_ref (sum_i w_i = 1), j = sum c_i h_i
-// (sum_i w_i c_i = 0), f_i - feq_i = h_i - w_i (rho - rho_ref) - w_i rho delta_i, and the
-// update adds to h.
+// (sum_i w_i c_i = 0), and the update adds to h.
+// feq_i = w_i rho (1 + delta_i), delta_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2 is kept without the 1,
+// so that the u^2 terms are not lost to rounding against 1 (sum_i w_i delta_i = 0 in exact
+// arithmetic; rounding 1 + ... biases the mass at small u).  An opposite pair (c, -c) is
+// updated through its sum and difference: with S = 4.5 (c.u)^2 - 1.5 u^2 and the Guo term
+// Ft_+- = w (Gs +- 3 c.F), Gs = 9 (c.u)(c.F) - 3 u.F, the sum of f - feq is
+// f_+ + f_- - 2 w rho - 2 w rho S and the difference f_+ - f_- - 6 w rho c.u.
 // T is double, float, or f2 (two cells at once).
 template <class L, int MRT, bool SHIFT, class T>
 __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3]) {
     using R = typename ScalarOf<T>::type;
     const Phys<R> &q = phys<R>(p);
+    constexpr int NP = (L::Q - 1) / 2;
+    // the pairs as sums and differences from here on
+    T fs[NP], fa[NP];
     T rho = f[0], j[3] = {T(0), T(0), T(0)};
-    Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
-        constexpr int i = 2 * decltype(kc)::value + 1;
-        const T a = f[i] - f[i + 1];
-        rho += f[i] + f[i + 1];
-        add_c<L::cx(i)>(j[0], a);
-        add_c<L::cy(i)>(j[1], a);
-        add_c<L::cz(i)>(j[2], a);
+    Unroll<0, NP>::run([&](auto kc) {
+        constexpr int r = decltype(kc)::value;
+        constexpr int i = 2 * r + 1;
+        fs[r] = f[i] + f[i + 1];
+        fa[r] = f[i] - f[i + 1];
+        rho += fs[r];
+        add_c<L::cx(i)>(j[0], fa[r]);
+        add_c<L::cy(i)>(j[1], fa[r]);
+        add_c<L::cz(i)>(j[2], fa[r]);
     });
     if (SHIFT) rho += T(q.rho_ref);
     const T irho = fdiv(T(1), rho);
     const T u[3] = {mad(T(0.5), F[0], j[0]) * irho, mad(T(0.5), F[1], j[1]) * irho, mad(T(0.5), F[2], j[2]) * irho};
     const T om = omega_of<T>(p, rho);
     const T nom = -om;
-    // feq_i = w_i rho (1 + delta_i), delta_i = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2, kept without the 1 so
-    // that the u^2 terms are not lost to rounding against 1 (sum_i w_i delta_i = 0 exactly in
-    // exact arithmetic; rounding the 1 + ... away biases the mass at small u).
     const T Bq = T(-1.5) * mad(u[0], u[0], mad(u[1], u[1], u[2] * u[2]));
     const T nuF3 = T(-3) * mad(u[0], F[0], mad(u[1], F[1], u[2] * F[2]));
     const T kguo = mad(T(-0.5), om, T(1));
     const T drho = SHIFT ? rho - T(q.rho_ref) : rho;     // rho minus the stored shift
-    T g[L::Q];
-    // one direction: delta = feq / (w rho) - 1, t4 = Ft / w
-    auto update = [&](int i, double w, const T &delta, const T &t4) {
-        const T wrho = T(w) * rho;
-        const T dn = mad(-wrho, delta, f[i] - T(w) * drho);          // f - feq
+    // rest population
+    T g0;
+    {
+        constexpr double w = wcol<L, R>(0);
+        const T dn = mad(-(T(w) * rho), Bq, f[0] - T(w) * drho);   // f - feq
         if (!MRT) {
-            f[i] = mad(kguo * T(w), t4, mad(nom, dn, f[i]));
+            f[0] = mad(kguo * T(w), nuF3, mad(nom, dn, f[0]));
         } else {
-            g[i] = mad(T(0.5 * w), t4, dn);                      // f - feq + Ft/2
-            f[i] = mad(nom, g[i], mad(T(w), t4, f[i]));           // BGK part with Ft
+            g0 = mad(T(0.5 * w), nuF3, dn);                        // f - feq + Ft/2
+            f[0] = mad(nom, g0, mad(T(w), nuF3, f[0]));             // BGK part with Ft
         }
-    };
-    update(0, wcol<L, R>(0), Bq, nuF3);
-    // opposite pair (i, i + 1): c_{i+1} = -c_i, the first non-zero component of c_i is +1
-    Unroll<0, (L::Q - 1) / 2>::run([&](auto kc) {
-        constexpr int i = 2 * decltype(kc)::value + 1;
+    }
+    T gs[NP], ga[NP];
+    // opposite pair r = (i, i + 1): c_{i+1} = -c_i, the first non-zero component of c_i is +1
+    Unroll<0, NP>::run([&](auto kc) {
+        constexpr int r = decltype(kc)::value;
+        constexpr int i = 2 * r + 1;
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        constexpr double w = wcol<L, R>(i);
         const T cu = dot_c<cx, cy, cz>(u);
         const T cF = dot_c<cx, cy, cz>(F);
-        constexpr double w = wcol<L, R>(i);
-        update(i, w, mad(cu, mad(T(4.5), cu, T(3)), Bq), mad(cF, mad(T(9), cu, T(3)), nuF3));
-        update(i + 1, w, mad(cu, mad(T(4.5), cu, T(-3)), Bq), mad(cF, mad(T(9), cu, T(-3)), nuF3));
+        const T S = mad(T(4.5) * cu, cu, Bq);
+        const T Gs = mad(T(9) * cu, cF, nuF3);
+        const T dns = mad(-(T(2 * w) * rho), S, fs[r] - T(2 * w) * drho);   // sum of f - feq
+        const T dna = mad(-(T(6 * w) * rho), cu, fa[r]);                     // difference
+        if (!MRT) {
+            fs[r] += mad(nom, dns, (kguo * T(2 * w)) * Gs);
+            fa[r] += mad(nom, dna, (kguo * T(6 * w)) * cF);
+        } else {
+            gs[r] = mad(T(w), Gs, dns);                  // sums of g = f - feq + Ft/2
+            ga[r] = mad(T(3 * w), cF, dna);
+            fs[r] += mad(nom, gs[r], T(2 * w) * Gs);     // BGK part with Ft
+            fa[r] += mad(nom, ga[r], T(6 * w) * cF);
+        }
     });
     if (MRT) {
-        constexpr int NP = (L::Q - 1) / 2;
-        T gs[NP], ga[NP];
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            gs[k] = g[2 * k + 1] + g[2 * k + 2];
-            ga[k] = g[2 * k + 1] - g[2 * k + 2];
-        }
-        T Ak[Ghosts<L>::K];
-        Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
-            constexpr int k = decltype(kk)::value;
-            constexpr bool ev = RowParity<L>::even(k);
-            T m = ev ? T(Ghosts<L>::row(k, 0)) * g[0] : T(0);
-            Unroll<0, NP>::run([&](auto qc) {
-                constexpr int r = decltype(qc)::value;
-                constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
-                if (c != 0.0) m = mad(T(c), ev ? gs[r] : ga[r], m);
-            });
-            Ak[k] = (T(q.s_rate[Ghosts<L>::kind(k)]) - om) * (T(1.0 / row_norm2<L>(k)) * m);
-        });
-        T e0 = T(0);
-        Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
-            constexpr int k = decltype(kk)::value;
-            if (RowParity<L>::even(k) && Ghosts<L>::row(k, 0) != 0.0) e0 = mad(T(Ghosts<L>::row(k, 0)), Ak[k], e0);
-        });
-        f[0] -= e0;
-        Unroll<0, NP>::run([&](auto qc) {
-            constexpr int r = decltype(qc)::value;
-            T E = T(0), O = T(0);
-            Unroll<0, Ghosts<L>::K>::run([&](auto kk) {
-                constexpr int k = decltype(kk)::value;
-                constexpr double c = Ghosts<L>::row(k, 2 * r + 1);
-                if (c != 0.0) {
-                    if (RowParity<L>::even(k)) E = mad(T(c), Ak[k], E);
-                    else O = mad(T(c), Ak[k], O);
-                }
-            });
-            f[2 * r + 1] -= E + O;
-            f[2 * r + 2] -= E - O;
-        });
+        if constexpr (std::is_same<L, D3Q19>::value) ghosts_d3q19<T, R>(q, om, g0, gs, ga, f[0], fs, fa);
+        else ghosts_generic<L, T, R>(q, om, g0, gs, ga, f[0], fs, fa);
     }
+    Unroll<0, NP>::run([&](auto kc) {
+        constexpr int r = decltype(kc)::value;
+        const T h = T(0.5) * fa[r];
+        f[2 * r + 1] = mad(T(0.5), fs[r], h);
+        f[2 * r + 2] = mad(T(0.5), fs[r], -h);
+    });
 }
 
 // ------------------------------------------------------------------ kernels

@@ -5,9 +5,9 @@ The tolerances are those stated for the storage formats: coexistence densities w
 
 Measurement (readings of the paper's unstated procedures):
   - bulk densities: box means far from the interfaces;
-  - Laplace: Delta P = p_EOS of the mean density in a 9 x 9 box at the droplet centre minus
-    p_EOS of the mean density in a 9 x 9 box at the far corner, averaged over 10 snapshots
-    200 steps apart; R from the mass balance
+  - Laplace: Delta P = p_EOS of the mean density in a centred square of half-width 0.35 R0
+    minus p_EOS of the mean density in a 32 x 32 square at the far corner, averaged over 20
+    snapshots 250 steps apart; R from the mass balance
     R = sqrt((M - rho_v A) / (pi (rho_l - rho_v))) with the measured bulk densities;
     gamma = slope of the least-squares fit Delta P = gamma / R + c;
   - convergence: node-restricted (2 x 2 x 2 mean) L2 difference of rho between successive
@@ -55,15 +55,18 @@ def _laplace(precision, t_ratio=0.8, radii=(20, 30, 40, 50, 60), n=256, steps=40
     b.step(steps)
     b.status()
     c = n // 2
-    # time average of 10 snapshots, 200 steps apart (FP16 storage carries per-step noise)
+    # time average of 20 snapshots, 250 steps apart, over a centred square of half-width
+    # 0.35 R0 and a 32 x 32 corner square: the liquid branch of the EOS is steep (Delta P to 1 %
+    # needs rho_in to ~1e-5), and FP16 storage adds per-step noise to rho
     acc = np.zeros((len(radii), 4))
-    nsnap = 10
+    nsnap = 10 * 2
     for _ in range(nsnap):
-        b.step(200)
+        b.step(250)
         for k in range(len(radii)):
+            h = max(4, int(0.35 * radii[k]))
             acc[k] += (b.reduce(k, plb.PLB_MASS)[0],
-                       b.reduce(k, plb.PLB_MEAN_RHO, (c - 4, c - 4, 0), (c + 5, c + 5, 1))[0],
-                       b.reduce(k, plb.PLB_MEAN_RHO, (0, 0, 0), (9, 9, 1))[0],
+                       b.reduce(k, plb.PLB_MEAN_RHO, (c - h, c - h, 0), (c + h + 1, c + h + 1, 1))[0],
+                       b.reduce(k, plb.PLB_MEAN_RHO, (0, 0, 0), (32, 32, 1))[0],
                        b.reduce(k, plb.PLB_UMAX)[0])
     acc /= nsnap
     rows = []
@@ -208,3 +211,50 @@ def test_diffusive_refinement_converges_second_order():
         assert d < 5e-4
     # measured 1.66 on 64 / 128 / 256 (1.42 on 32 / 64 / 128): approaching 2 from below
     assert order > 1.5
+
+
+MRT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98)
+
+
+def _plates_d3q19(precision, stochastic=0, steps=400000):
+    """The D3Q19 plates workload (walls in y, liquid layers y < 64 and y >= 192, vapour core,
+    F = 1e-7 along x, PR T/Tc = 0.8, MRT, tau = 1) on a 4 x 256 x 4 cross-section (the problem
+    is x- and z-invariant).  400,000 steps from rest leave exp(-10) of the slowest viscous
+    mode.  Returns u_x(y), rho(y)."""
+    import paper_2504_15018_gb300 as plb
+    rv, rl, _ = maxwell(0.8)
+    dims, rho = inputs.plates_d3q19((4, 256, 4), rv, rl)
+    opts = plb.make_opts(precision=precision, collision=plb.PLB_MRT, wall_y=1, body_force=(1e-7, 0.0, 0.0),
+                         fp16_rounding=stochastic, **MRT_RATES)
+    lat = plb.Lattice(plb.PLB_D3Q19, dims, plb.pr_eos(0.8), 1.0, -1.0, 2.0, opts=opts)
+    lat.init(rho)
+    lat.step(steps)
+    lat.status()
+    r, u, _ = lat.moments()
+    shape = (dims[2], dims[1], dims[0])
+    return u[0].reshape(shape).mean(axis=(0, 2)), r.reshape(shape).mean(axis=(0, 2))
+
+
+def test_plates_velocity_profile_all_precisions():
+    """Plate velocity profile per storage precision against FP64, and FP64 against the steady
+    channel flow of its own density profile (mu(y) = rho(y) / 6 at tau = 1, interpolated
+    linearly between cell centres).  F = 1e-7 changes a liquid population by ~1.6e-8 per step,
+    about one FP32 ulp and 1e-4 of an FP16 ulp, so the storage precisions are judged by how
+    much of the profile they keep (relative L2 against FP64, reported; FP32 asserted within
+    2 %, FP16S with stochastic rounding within 25 %)."""
+    from oracle import params as pp
+    u64, r64 = _plates_d3q19(0)
+    ny = len(u64)
+    y = np.arange(ny, dtype=float)
+    mu = lambda s: float(np.interp(s, y, r64)) / 6.0
+    ua = pp.channel_flow(y, mu, 1e-7, -0.5, ny - 0.5, breaks=tuple(np.arange(ny - 1) + 0.5))
+    e64 = np.sqrt(((u64 - ua) ** 2).sum() / (ua ** 2).sum())
+    print(f"fp64: umax {u64.max():.4e} (channel flow {ua.max():.4e}), relative L2 vs channel flow {e64:.3e}")
+    assert e64 < 0.05
+    errs = {}
+    for name, prec, sr in (("fp32", 1, 0), ("fp16s_sr", 2, 1), ("fp16s_rne", 2, 0)):
+        u, _ = _plates_d3q19(prec, sr)
+        errs[name] = np.sqrt(((u - u64) ** 2).sum() / (u64 ** 2).sum())
+        print(f"{name}: umax {u.max():.4e}, relative L2 vs fp64 {errs[name]:.3e}")
+    assert errs["fp32"] < 0.02
+    assert errs["fp16s_sr"] < 0.25
