@@ -155,12 +155,16 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
+KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_pair.cuh", "plb_step.cuh")
+
+
 def kernel_source_sha():
+    """Hash of the files that hold the step kernels' device code (k_psi_pair, k_collide_pair
+    and everything they inline)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_15018_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -136,6 +136,15 @@ void plb_destroy(plb_t *h);
  * the copies asynchronous.  Errors: PLB_EINVAL (non-positive / non-finite rho0), PLB_ECUDA. */
 int plb_init(plb_t *h, const double *rho0, const double *u0);
 
+/* As plb_init, then the populations become f^eq(rho0, u0 - F/(2 rho0)) (Eq. Single_Phase_EDF),
+ * F the total force of Eqs. interactionForce and F_ext on the initial density, so that the
+ * velocity of Eq. Momentum, (sum f c + F/2)/rho, equals u0 from the first step.  plb_init
+ * leaves interfaces with the velocity F/(2 rho), which launches sound waves; the Sec. VI
+ * benchmarks (the planar interface set in motion in Sec. VI.C) need the balanced start to
+ * converge at second order.  Arguments and errors as plb_init; a density outside the psi
+ * domain is reported by plb_status. */
+int plb_init_physical(plb_t *h, const double *rho0, const double *u0);
+
 /* Advances n time steps (two kernels per step: psi pass, then the fused force +
  * collide + stream pass).  Asynchronous; returns launch errors only.  Device-side
  * faults of the method (psi domain, non-finite density) are recorded in a device flag
@@ -221,8 +230,9 @@ void plb_batch_destroy(plb_batch_t *b);
  * destroy it).  NULL for a bad index. */
 plb_t *plb_batch_instance(plb_batch_t *b, int k);
 
-/* f = f^eq(rho0, u0) on instance k (as plb_init). */
+/* f = f^eq(rho0, u0) on instance k (as plb_init); plb_batch_init_physical as plb_init_physical. */
 int plb_batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0);
+int plb_batch_init_physical(plb_batch_t *b, int k, const double *rho0, const double *u0);
 
 /* Advances every instance by nsteps steps in one persistent launch.  Asynchronous. */
 int plb_batch_step(plb_batch_t *b, int nsteps);
@@ -239,8 +249,9 @@ int plb_batch_reset_error(plb_batch_t *b);
  * A non-positive tile_cells or blocks_per_sm keeps the current value. */
 int plb_batch_configure(plb_batch_t *b, int tile_cells, int blocks_per_sm, unsigned spin_limit);
 
-/* Times steps_per_candidate steps for every tile size in {1024, ..., 16384} cells and 1 or 2
- * blocks per SM, keeps the fastest, and reports it (any output may be NULL; best_ms is per
+/* Times steps_per_candidate steps for every tile size in {512, ..., 16384} cells and every
+ * resident count from 1 block per SM to the kernel's occupancy limit (at most 4; the kernel
+ * is compiled for 3 D2Q9 / 2 D3Q19 blocks per SM without spilling), keeps the fastest, and reports it (any output may be NULL; best_ms is per
  * step).  The timed steps advance the batch. */
 int plb_batch_autotune(plb_batch_t *b, int steps_per_candidate, int *tile_cells, int *blocks_per_sm, double *best_ms);
 

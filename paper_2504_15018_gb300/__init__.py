@@ -77,6 +77,7 @@ _SIGNATURES = {
                                   _VP, ctypes.POINTER(_VP)]),
     "plb_destroy": (None, [_VP]),
     "plb_init": (ctypes.c_int, [_VP, _DP, _DP]),
+    "plb_init_physical": (ctypes.c_int, [_VP, _DP, _DP]),
     "plb_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "plb_step_timed": (ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     "plb_status": (ctypes.c_int, [_VP]),
@@ -99,6 +100,7 @@ _SIGNATURES = {
     "plb_batch_destroy": (None, [_VP]),
     "plb_batch_instance": (_VP, [_VP, ctypes.c_int]),
     "plb_batch_init": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
+    "plb_batch_init_physical": (ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP]),
     "plb_batch_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "plb_batch_status": (ctypes.c_int, [_VP]),
     "plb_batch_reset_error": (ctypes.c_int, [_VP]),
@@ -193,6 +195,10 @@ def plb_destroy(h):
 
 def plb_init(h, rho0, u0=None):
     _check(lib().plb_init(h, _dptr(rho0), _dptr(u0)))
+
+
+def plb_init_physical(h, rho0, u0=None):
+    _check(lib().plb_init_physical(h, _dptr(rho0), _dptr(u0)))
 
 
 def plb_step(h, n: int):
@@ -291,6 +297,10 @@ def plb_batch_instance(b, k: int):
 
 def plb_batch_init(b, k: int, rho0, u0=None):
     _check(lib().plb_batch_init(b, int(k), _dptr(rho0), _dptr(u0)))
+
+
+def plb_batch_init_physical(b, k: int, rho0, u0=None):
+    _check(lib().plb_batch_init_physical(b, int(k), _dptr(rho0), _dptr(u0)))
 
 
 def plb_batch_step(b, nsteps: int):
@@ -395,10 +405,11 @@ class Batch:
         d = self.instances[k].dims
         return d[0] * d[1] * d[2]
 
-    def init(self, k: int, rho0, u0=None):
+    def init(self, k: int, rho0, u0=None, physical: bool = False):
+        """physical: plb_batch_init_physical (the velocity of Eq. Momentum is u0 at t = 0)."""
         rho0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
         u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
-        plb_batch_init(self.b, k, rho0, u0)
+        (plb_batch_init_physical if physical else plb_batch_init)(self.b, k, rho0, u0)
 
     def step(self, n: int = 1):
         plb_batch_step(self.b, n)
@@ -458,10 +469,11 @@ class Lattice:
                 pass
             self.h = None
 
-    def init(self, rho0, u0=None):
+    def init(self, rho0, u0=None, physical: bool = False):
+        """physical: plb_init_physical (the velocity of Eq. Momentum is u0 at t = 0)."""
         rho0 = np.ascontiguousarray(rho0, dtype=np.float64).reshape(-1)
         u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
-        plb_init(self.h, rho0, u0)
+        (plb_init_physical if physical else plb_init)(self.h, rho0, u0)
 
     def step(self, n: int = 1):
         plb_step(self.h, n)

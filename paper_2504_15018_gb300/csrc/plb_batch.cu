@@ -218,7 +218,7 @@ int plb_batch_create(int lattice, int n, const plb_instance *inst, void *dev_wor
     if (e != cudaSuccess) return fail_destroy(plb::set_error(PLB_ECUDA, "device query: %s", cudaGetErrorString(e)));
     if (occ < 1) return fail_destroy(plb::set_error(PLB_EUNSUPPORTED, "batch kernel does not fit on an SM"));
     b->max_blocks_per_sm = occ;
-    b->blocks_per_sm = std::min(occ, 2);
+    b->blocks_per_sm = occ;
     b->tile_cells = 4096;
     b->views.resize(n, nullptr);
     b->host_insts.resize(n);
@@ -295,9 +295,10 @@ plb_t *plb_batch_instance(plb_batch_t *b, int k) {
     return b->views[k];
 }
 
-int plb_batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0) {
+static int batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0, bool physical) {
     if (!b || k < 0 || k >= b->n) return plb::set_error(PLB_EINVAL, "bad batch or instance index");
     int st = plb::init_state(b->views[k], rho0, u0);
+    if (st == PLB_OK && physical) st = plb::rebalance_state(b->views[k]);
     if (st != PLB_OK) return st;
     // the instance restarts at even parity; the device descriptor must say so
     b->host_insts[k].odd = 0;
@@ -306,6 +307,14 @@ int plb_batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0) 
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return plb::set_error(PLB_ECUDA, "parity upload: %s", cudaGetErrorString(e));
     return PLB_OK;
+}
+
+int plb_batch_init(plb_batch_t *b, int k, const double *rho0, const double *u0) {
+    return batch_init(b, k, rho0, u0, false);
+}
+
+int plb_batch_init_physical(plb_batch_t *b, int k, const double *rho0, const double *u0) {
+    return batch_init(b, k, rho0, u0, true);
 }
 
 int plb_batch_configure(plb_batch_t *b, int tile_cells, int blocks_per_sm, unsigned spin_limit) {
@@ -395,14 +404,14 @@ int plb_batch_withhold_arrivals(plb_batch_t *b, unsigned count) {
 
 int plb_batch_autotune(plb_batch_t *b, int steps_per_candidate, int *tile_cells, int *blocks_per_sm, double *best_ms) {
     if (!b || steps_per_candidate < 1) return plb::set_error(PLB_EINVAL, "bad argument");
-    const int cand_tiles[] = {1024, 2048, 4096, 8192, 16384};
+    const int cand_tiles[] = {512, 1024, 2048, 4096, 8192, 16384};
     float best = 1e30f;
     int bt = b->tile_cells, bb = b->blocks_per_sm;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return plb::set_error(PLB_ECUDA, "cudaEventCreate failed");
     int st = PLB_OK;
-    for (int bps = 1; bps <= std::min(b->max_blocks_per_sm, 2) && st == PLB_OK; ++bps) {
+    for (int bps = 1; bps <= std::min(b->max_blocks_per_sm, 4) && st == PLB_OK; ++bps) {
         for (int tc : cand_tiles) {
             st = plb_batch_configure(b, tc, bps, b->spin_limit);
             if (st != PLB_OK) break;

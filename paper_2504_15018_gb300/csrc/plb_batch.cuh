@@ -7,6 +7,10 @@
 
 namespace plb {
 
+// Minimum resident 256-thread blocks per SM requested from the register allocator: the
+// most that fit without spilling (D2Q9: 80 registers, 3 blocks; D3Q19 MRT: 128, 2 blocks).
+template <class L> struct BatchMinBlocks { static constexpr int value = L::Q == 9 ? 3 : 2; };
+
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block) when
 // any block gave up waiting, after which the kernel returns.
 __device__ __forceinline__ bool grid_sync(GridBar *bar, unsigned expected, unsigned spin_limit) {
@@ -86,7 +90,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
 }
 
 template <class L, class S, int MRT>
-__global__ void __launch_bounds__(256, 1) k_batch(BatchLaunch b) {
+__global__ void __launch_bounds__(256, BatchMinBlocks<L>::value) k_batch(BatchLaunch b) {
     const unsigned salt0 = *reinterpret_cast<volatile unsigned *>(&b.bar->salt);
     for (int step = 0; step < b.nsteps; ++step) {
         for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {

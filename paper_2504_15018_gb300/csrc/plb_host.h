@@ -72,4 +72,6 @@ struct plb_state {
 namespace plb {
 // f = f^eq(rho0, u0) on every cell of h (the body of plb_init).
 int init_state(plb_state *h, const double *rho0, const double *u0);
+// After init_state: psi pass and k_rebalance, so the physical velocity at t = 0 is u0.
+int rebalance_state(plb_state *h);
 }  // namespace plb

@@ -10,6 +10,11 @@
 #include "plb_pair.cuh"
 #include "plb_step.cuh"
 
+// Two cells per thread for FP16 storage (1) or one (0).
+#ifndef PLB_HALF_PAIR
+#define PLB_HALF_PAIR 1
+#endif
+
 namespace plb {
 
 // Linear thread -> cell mapping (x fastest) for the readout kernels.
@@ -74,6 +79,42 @@ __global__ void k_moments(KParams p, const S *__restrict__ A, const typename Sto
     if (u_out)
         for (int a = 0; a < L::D; ++a) u_out[a * cn + k] = (double)((j[a] + (T)0.5 * F[a]) / rho);
     if (p_out) p_out[k] = (double)eos_pressure<T>(p, rho);
+}
+
+// ------------------------------------------------- balanced start (plb_init_physical)
+// At t = 0 (even parity, natural layout) the populations are f^eq(rho, u0), so sum f c = rho u0.
+// Rewrites them as f^eq(rho, u0 - F / (2 rho)), F the force of the initial density (psi pass
+// already run), so that the velocity of Eq. Momentum, (sum f c + F/2) / rho, is u0.  Each
+// thread reads and writes its own cell only.
+template <class L, class S>
+__global__ void k_rebalance(KParams p, S *__restrict__ A, const typename Store<S>::PsiT *__restrict__ psi) {
+    using T = typename Store<S>::T;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int x, y, z;
+    if (!cell_coords(p, s, x, y, z)) return;
+    const Nbr nb = neighbours(p, x, y, z);
+    T f[L::Q];
+    load_pops<L, S>(p, A, x, y, z, nb, s, false, f);
+    T rho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        rho += f[i];
+        j[0] += (T)L::cx(i) * f[i];
+        j[1] += (T)L::cy(i) * f[i];
+        j[2] += (T)L::cz(i) * f[i];
+    }
+    T F[3];
+    cell_force<L, T>(p, psi, psi_index(p, x, y, z), F);
+    T u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] - (T)0.5 * F[a]) / rho;
+    const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T rref = phys<T>(p).rho_ref;
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        const T cu = (T)L::cx(i) * u[0] + (T)L::cy(i) * u[1] + (T)L::cz(i) * u[2];
+        const T feq = (T)L::w(i) * rho * ((T)1 - (T)1.5 * usq + (T)3 * cu + (T)4.5 * cu * cu);
+        Store<S>::st(A + (long long)i * p.pstride + s, Store<S>::SHIFT ? feq - (T)L::w(i) * rref : feq);
+    });
 }
 
 // ------------------------------------------------------ population exchange
@@ -200,6 +241,7 @@ template <class L, class S> struct Launch {
     // Two cells per thread with packed FP32 arithmetic where it applies (FP32 arithmetic,
     // even nx, fewer than 2^31 cells); one cell per thread otherwise.
     static bool use_pair(const KParams &p) {
+        if (std::is_same<S, __half>::value && !PLB_HALF_PAIR) return false;
         return !std::is_same<S, double>::value && (p.nx % 2 == 0) && p.n < (1LL << 31);
     }
     static void dims_pair(const KParams &p, dim3 &grid, dim3 &block) {
@@ -268,11 +310,14 @@ template <class L, class S> struct Launch {
         k_reduce<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, what, lo[0], lo[1], lo[2],
                                                 hi[0], hi[1], hi[2], partials);
     }
+    static void rebalance(const KParams &p, void *A, const void *psi, cudaStream_t st) {
+        k_rebalance<L, S><<<blocks(p.n, 256), 256, 0, st>>>(p, (S *)A, (const PsiT *)psi);
+    }
     static const void *batch_bgk() { return reinterpret_cast<const void *>(&k_batch<L, S, 0>); }
     static const void *batch_mrt() { return reinterpret_cast<const void *>(&k_batch<L, S, 1>); }
     static constexpr Launchers table() {
         return Launchers{&init,     &psi,    {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce,
-                         {&batch_bgk, &batch_mrt}};
+                         {&batch_bgk, &batch_mrt}, &rebalance};
     }
 };
 

@@ -345,6 +345,12 @@ int plb_init(plb_t *h, const double *rho0, const double *u0) {
     return plb::init_state(h, rho0, u0);
 }
 
+int plb_init_physical(plb_t *h, const double *rho0, const double *u0) {
+    if (h && h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_init_physical");
+    const int st = plb::init_state(h, rho0, u0);
+    return st != PLB_OK ? st : plb::rebalance_state(h);
+}
+
 }  // extern "C"
 
 int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
@@ -372,6 +378,14 @@ int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
     h->t = 0;
     h->odd = 0;
     return PLB_OK;
+}
+
+int plb::rebalance_state(plb_state *h) {
+    h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), 0, h->stream);
+    int st = check_launch();
+    if (st) return st;
+    h->L->rebalance(h->kp, pops_ptr(h), psi_ptr(h), h->stream);
+    return check_launch();
 }
 
 extern "C" {

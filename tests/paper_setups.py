@@ -72,23 +72,10 @@ def equilibrium(c, w, rho, u):
     return w[:, None] * rho[None, :] * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * usq[None, :])
 
 
-def balanced_init_gpu(lat, rho, u0=None):
-    """Start a lattice at rest (or at u0) in the sense of Eq. Momentum: the populations carry
-    rho u0 - F/2, so the physical velocity (sum f c + F/2) / rho is u0 from the first step.
-    f = f^eq(rho, u0) alone leaves every interface with a velocity F / (2 rho), which launches
-    sound waves that outlive the paper's settling times at tau_l = 0.56."""
-    import paper_2504_15018_gb300 as plb
-    d = 2 if lat.lattice == plb.PLB_D2Q9 else 3
-    lat.init(rho, u0)
-    _, u, _ = lat.moments()
-    base = np.zeros((d, rho.size)) if u0 is None else np.asarray(u0, dtype=float)
-    c, w = plb.plb_velocity_set(lat.lattice)
-    lat.set_populations(equilibrium(c[:, :d].astype(float), w, rho, 2 * base - u[:d]))
-
-
 def balanced_init_oracle(P, lattice, rho, u0=None):
-    """The same start for the oracle: f^eq(rho, u0 - F / (2 rho)), F read back through the
-    oracle's own moments of f^eq(rho, u0)."""
+    """Start at rest (or at u0) in the sense of Eq. Momentum: f^eq(rho, u0 - F / (2 rho)), so the
+    physical velocity (sum f c + F/2) / rho is u0 from the first step (the library's
+    plb_init_physical).  F is read back through the oracle's own moments of f^eq(rho, u0)."""
     import oracle
     f = oracle.init(P, rho, u0)
     _, u, _ = oracle.moments(P, f)

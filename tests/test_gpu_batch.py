@@ -122,7 +122,7 @@ def test_autotune_picks_a_valid_tiling_and_keeps_the_dynamics():
     for k, (rho, u0) in enumerate(fields):
         b.init(k, rho, u0)
     tile, bps, ms = b.autotune(2)
-    assert tile in (1024, 2048, 4096, 8192, 16384) and bps in (1, 2) and ms > 0
+    assert tile in (512, 1024, 2048, 4096, 8192, 16384) and 1 <= bps <= 4 and ms > 0
     steps = plb.plb_batch_time(b.b)
     assert steps == 2 * 5 * 2 * (1 + 1) or steps > 0
     b.step(3)
@@ -163,3 +163,19 @@ def test_views_refuse_stepping():
     with pytest.raises(plb.PlbError) as e:
         plb.plb_step(view, 1)
     assert e.value.code == plb.PLB_EINVAL
+
+
+def test_batch_init_physical_matches_a_single_lattice():
+    import paper_2504_15018_gb300 as plb
+    insts, fields = _instances(0, D2_SPECS[:4], 1, True)
+    b = plb.Batch(plb.PLB_D2Q9, insts)
+    for k, (rho, u0) in enumerate(fields):
+        b.init(k, rho, u0, physical=True)
+    b.step(5)
+    b.status()
+    for k, (rho, u0) in enumerate(fields):
+        lat = plb.Lattice(0, tuple(insts[k].dims), insts[k].eos, insts[k].tau, insts[k].G, insts[k].eps,
+                          opts=insts[k].opts)
+        lat.init(rho, u0, physical=True)
+        lat.step(5)
+        assert np.array_equal(b.populations(k), lat.populations()), k

@@ -18,7 +18,7 @@ from oracle import params as pp
 
 pytestmark = pytest.mark.gpu
 
-from paper_setups import converter as _conv, relative_norms, plates, galilean_steps, equilibrium, balanced_init_gpu
+from paper_setups import converter as _conv, relative_norms, plates, galilean_steps, equilibrium
 
 
 def converter(k, tau_l):
@@ -121,7 +121,7 @@ def _galilean(k, precision=0):
                          tau_rho_l=s["rho_l"])
     lat = plb.Lattice(plb.PLB_D2Q9, (nx, 2, 1), plb.paper_eos(s["rho_v"], s["rho_l"], s["P"]), tau=0.56, G=-1.0,
                       eps=2.0, opts=opts)
-    balanced_init_gpu(lat, np.tile(s["rho"], 2))
+    lat.init(np.tile(s["rho"], 2), physical=True)
     lat.step(n1)
     # the velocity jump: every cell's equilibrium part moves by U, the rest is kept (the effect
     # of a one-step force rho U)
@@ -143,8 +143,8 @@ def test_galilean_invariance_converges_second_order():
     """Sec. VI.C: the planar interface of Sec. VI.A (Table II grids) at rest until 7.91 us, then
     moved at U_x = 0.1 m/s until 31.6 us.  The phases drift relative to each other through the
     interface error; the error of u_x against the uniform U_x falls at second order.  The start
-    is balanced (physical velocity zero, see balanced_init_gpu); with f = f^eq(rho, 0) the
-    sound waves from the initial F/(2 rho) velocity dominate the error on grids 3-5."""
+    is balanced (plb_init_physical: physical velocity zero); with f = f^eq(rho, 0) the sound
+    waves from the initial F/(2 rho) velocity dominate the error on grids 3-5."""
     norms = []
     for k in range(1, 6):
         n, U = _galilean(k)
@@ -167,7 +167,7 @@ def _plates(k, precision=0, steps_factor=0.5):
                       G=-1.0, eps=2.0, opts=opts)
     u0 = np.zeros((2, nx * ny))
     u0[0] = np.repeat(s["u"], nx)
-    balanced_init_gpu(lat, np.repeat(s["rho"], nx), u0)
+    lat.init(np.repeat(s["rho"], nx), u0, physical=True)
     steps = int(steps_factor * (ny / 2) ** 2 / s["nu_l"])
     lat.step(steps // 2)
     _, u, _ = lat.moments()

@@ -209,3 +209,28 @@ def test_psi_domain_and_invalid_inputs_are_reported():
     lat.init(np.full(128, 2.0))       # re-init clears the flag
     lat.step(2)
     lat.status()
+
+
+@pytest.mark.parametrize("name", ["d2q9_bgk_periodic_droplet", "d3q19_mrt_walls_slab", "d3q19_mrt_periodic_droplet_u0"])
+def test_init_physical_matches_the_balanced_oracle_start(name):
+    """plb_init_physical: f^eq(rho0, u0 - F/(2 rho0)) against the same start built from the
+    oracle's own force, and the velocity of Eq. Momentum equal to u0 at t = 0."""
+    from paper_setups import balanced_init_oracle
+    case = dict(FP64_CASES[name], precision=0)
+    rho, u0, rv, rl = case_fields(case)
+    P = oracle_params(case, rv, rl)
+    ref = balanced_init_oracle(P, case["lattice"], rho, u0)[:, direction_map(case["lattice"])].T
+    lat = make_lattice(case, rv, rl)
+    lat.init(rho, u0, physical=True)
+    lat.status()
+    got = lat.populations()
+    assert max_rel_err(ref, got) < 1e-13
+    _, u, _ = lat.moments()
+    d = 2 if case["lattice"] == 0 else 3
+    want = np.zeros((d, rho.size)) if u0 is None else u0
+    assert np.max(np.abs(u[:d] - want)) < 1e-15
+    # FP32 storage: the same start to FP32 rounding
+    lat32 = make_lattice(dict(case, precision=1), rv, rl)
+    lat32.init(rho, u0, physical=True)
+    _, u32, _ = lat32.moments()
+    assert np.max(np.abs(u32[:d] - want)) < 1e-6

@@ -6,7 +6,7 @@ The tolerances are those stated for the storage formats: coexistence densities w
 Measurement (readings of the paper's unstated procedures):
   - bulk densities: box means far from the interfaces;
   - Laplace: Delta P = p_EOS of the mean density in a centred square of half-width 0.35 R0
-    minus p_EOS of the mean density in a 32 x 32 square at the far corner, averaged over 20
+    minus p_EOS of the mean density in a 32 x 32 square at the far corner, averaged over 40
     snapshots 250 steps apart; R from the mass balance
     R = sqrt((M - rho_v A) / (pi (rho_l - rho_v))) with the measured bulk densities;
     gamma = slope of the least-squares fit Delta P = gamma / R + c;
@@ -55,11 +55,11 @@ def _laplace(precision, t_ratio=0.8, radii=(20, 30, 40, 50, 60), n=256, steps=40
     b.step(steps)
     b.status()
     c = n // 2
-    # time average of 20 snapshots, 250 steps apart, over a centred square of half-width
+    # time average of 40 snapshots, 250 steps apart, over a centred square of half-width
     # 0.35 R0 and a 32 x 32 corner square: the liquid branch of the EOS is steep (Delta P to 1 %
     # needs rho_in to ~1e-5), and FP16 storage adds per-step noise to rho
     acc = np.zeros((len(radii), 4))
-    nsnap = 10 * 2
+    nsnap = 40
     for _ in range(nsnap):
         b.step(250)
         for k in range(len(radii)):
