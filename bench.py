@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--precision", default="fp32", choices=list(PREC))
     ap.add_argument("--collision", default="mrt", choices=["mrt", "bgk"])
+    ap.add_argument("--streaming", default="aa", choices=["aa", "fused"],
+                    help="fused: one kernel per step, two population copies; aa: two kernels, in place")
     ap.add_argument("--dims", default="512x256x256")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="plates", choices=["plates", "batch96"],
@@ -86,10 +88,13 @@ def workload_name(dims, precision, collision):
     return f"d3q19_plates_{dims[0]}x{dims[1]}x{dims[2]}_{precision}_{collision}_pr0.8"
 
 
-def bytes_per_cell(precision, q=19):
-    """Algorithmic bytes per cell update of the two-pass step: psi pass reads Q
-    populations and writes psi; the fused pass reads Q populations and psi, writes Q."""
+def bytes_per_cell(precision, q=19, streaming="aa"):
+    """Algorithmic bytes per cell update.  Two-pass step: the psi pass reads Q populations and
+    writes psi; the fused pass reads Q populations and psi, writes Q.  Single pass: Q
+    populations read and Q written (psi stays on chip; halo re-reads are not algorithmic)."""
     sp, sq = POP_BYTES[precision], PSI_BYTES[precision]
+    if streaming == "fused":
+        return dict(psi_pass=0, fused_pass=2 * q * sp, step=2 * q * sp)
     return dict(psi_pass=q * sp + sq, fused_pass=2 * q * sp + sq, step=3 * q * sp + 2 * sq)
 
 
@@ -98,12 +103,12 @@ def initial_density(dims, rho_v, rho_l):
     return inputs.plates_d3q19(dims, rho_v, rho_l)[1]
 
 
-def make_lattice(dims, precision, collision):
+def make_lattice(dims, precision, collision, streaming="aa"):
     import paper_2504_15018_gb300 as plb
     eos = plb.pr_eos(T_RATIO)
     opts = plb.make_opts(precision=PREC[precision], collision=plb.PLB_MRT if collision == "mrt" else plb.PLB_BGK,
                          wall_y=1, body_force=(BODY_FORCE, 0.0, 0.0), fp16_rounding=int(precision == "fp16s_sr"),
-                         **MRT_RATES)
+                         streaming=int(streaming == "fused"), **MRT_RATES)
     return plb.Lattice(plb.PLB_D3Q19, dims, eos, tau=1.0, G=-1.0, eps=2.0, opts=opts)
 
 
@@ -155,12 +160,12 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_pair.cuh", "plb_step.cuh")
+KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_pair.cuh", "plb_step.cuh")
 
 
 def kernel_source_sha():
-    """Hash of the files that hold the step kernels' device code (k_psi_pair, k_collide_pair
-    and everything they inline)."""
+    """Hash of the files that hold the step kernels' device code (k_psi_pair, k_collide_pair,
+    k_fused_pair and everything they inline)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_15018_gb300", "csrc")
     for f in KERNEL_SOURCES:
@@ -168,9 +173,9 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per fused-pass launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def recorded_traffic(workload, kernel):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     if not os.path.exists(path):
         return None
@@ -178,7 +183,7 @@ def recorded_traffic(workload):
     sha = re.search(r"kernel_source_sha:\s*(\w+)", text)
     if not sha or sha.group(1) != kernel_source_sha():
         return None
-    m = re.search(re.escape(workload) + r"\s*\|\s*([0-9.eE+]+)", text)
+    m = re.search(re.escape(workload) + r"\s*\|\s*" + re.escape(kernel) + r"\s*\|\s*([0-9.eE+]+)", text)
     return float(m.group(1)) if m else None
 
 
@@ -222,7 +227,9 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    lat = make_lattice(dims, args.precision, args.collision)
+    if args.precision == "fp64":
+        args.streaming = "aa"            # the single pass needs FP32 arithmetic
+    lat = make_lattice(dims, args.precision, args.collision, args.streaming)
     lat.init(rho0)
     lat.step(max(args.warmup, 3))
     lat.status()
@@ -240,21 +247,24 @@ def run_gpu(args):
     # roofline of the dominant kernel (fused pass), per-launch events on the same stream
     nprof = min(args.steps, 20)
     ms_psi, ms_fused = lat.step_timed(nprof)
-    bpc = bytes_per_cell(args.precision)
+    bpc = bytes_per_cell(args.precision, streaming=args.streaming)
     fused_gbs = bpc["fused_pass"] * ncell * nprof / (ms_fused / 1e3) / 1e9
-    psi_gbs = bpc["psi_pass"] * ncell * nprof / (ms_psi / 1e3) / 1e9
     peak, peak_kind = peak_hbm()
     wl = workload_name(dims, args.precision, args.collision)
-    traffic = recorded_traffic(wl)
-    roofline = {"bound": "hbm", "kernel": "k_collide (fused force + collide + stream)",
+    kernel = ("k_fused_pair (psi of tile + halo in shared memory, force, collide, push stream)"
+              if args.streaming == "fused" else "k_collide_pair (fused force + collide + stream)")
+    traffic = recorded_traffic(wl, kernel.split()[0])
+    roofline = {"bound": "hbm", "kernel": kernel,
                 "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(fused_gbs / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": bpc["fused_pass"] * ncell,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "psi_pass_gbs": round(psi_gbs, 1), "psi_pass_frac": round(psi_gbs / peak, 4),
                 "step_gbs": round(value / world * bpc["step"], 1),
                 "step_frac": round(value / world * bpc["step"] / peak, 4),
                 "time_share_fused": round(ms_fused / (ms_fused + ms_psi), 3)}
+    if ms_psi > 0:
+        psi_gbs = bpc["psi_pass"] * ncell * nprof / (ms_psi / 1e3) / 1e9
+        roofline.update(psi_pass_gbs=round(psi_gbs, 1), psi_pass_frac=round(psi_gbs / peak, 4))
 
     # e2e through the public API with pinned host buffers: upload rho0, run, read fields back
     e2e = None
@@ -283,10 +293,12 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants:
-        for prec in ("fp16s", "fp16s_sr", "fp64", "fp32"):
-            if prec == args.precision:
+        combos = [("fp16s", "fused"), ("fp16s_sr", "fused"), ("fp32", "fused"), ("fp32", "aa"), ("fp16s", "aa"),
+                  ("fp64", "aa")]
+        for prec, strm in combos:
+            if (prec, strm) == (args.precision, args.streaming):
                 continue
-            lv = make_lattice(dims, prec, args.collision)
+            lv = make_lattice(dims, prec, args.collision, strm)
             lv.init(rho0)
             lv.step(3)
             nst = 20 if prec != "fp64" else 6
@@ -294,9 +306,11 @@ def run_gpu(args):
             lv.status()
             g = ncell * nst / tv / 1e9
             ms_p, ms_f = lv.step_timed(min(nst, 6))
-            bpv = bytes_per_cell(prec)
-            variants[prec] = {"glups": round(g, 3), "step_frac_hbm": round(g * bpv["step"] / peak, 4),
-                              "fused_frac_hbm": round(bpv["fused_pass"] * ncell * min(nst, 6) / (ms_f / 1e3) / 1e9 / peak, 4)}
+            bpv = bytes_per_cell(prec, streaming=strm)
+            variants[f"{prec}_{strm}"] = {
+                "glups": round(g, 3), "step_frac_hbm": round(g * bpv["step"] / peak, 4),
+                "dominant_kernel_frac_hbm": round(bpv["fused_pass"] * ncell * min(nst, 6) / (ms_f / 1e3) / 1e9 / peak, 4),
+                "bytes_per_cell": bpv["step"]}
             del lv
             torch.cuda.empty_cache()
 
@@ -310,11 +324,13 @@ def run_gpu(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
                 "data": "synthetic (seeded tanh liquid-vapour layers, Maxwell densities of the PR EOS)",
                 "config": {"workload": wl, "cells": ncell, "lattice": "D3Q19", "collision": args.collision,
-                           "precision": args.precision, "eos": "Peng-Robinson a=2/49 b=2/21 w=0.327 T/Tc=0.8",
+                           "precision": args.precision, "streaming": args.streaming,
+                           "bytes_per_cell": bpc["step"], "eos": "Peng-Robinson a=2/49 b=2/21 w=0.327 T/Tc=0.8",
                            "boundaries": "halfway bounce-back walls in y, periodic x and z",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (populations %.2f GB)" % (19 * POP_BYTES[args.precision] * ncell / 1e9)},
-                "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": (1 if args.streaming == "fused" else 2) * args.steps,
                 "cpu_baseline": cpu, "variants": variants or None}
         print(json.dumps(line))
     if world > 1:

@@ -101,7 +101,16 @@ typedef struct plb_opts {
     double body_force[3];    /* external force density F_ext added to F (Sec. II) [0] */
     int fp16_rounding;       /* PLB_FP16S stores: 0 round to nearest even; 1 stochastic rounding
                                 (unbiased: no drift from repeated rounding, no stagnation) [0] */
+    int streaming;           /* PLB_STREAM_AA: two kernels per step (psi pass, fused force/collide/
+                                stream) on one in-place population copy (AA pattern).
+                                PLB_STREAM_FUSED: one kernel per step that forms psi of each tile and
+                                its halo in shared memory, collides and pushes into a second copy of
+                                the populations (twice the population memory, about 30 % fewer DRAM
+                                bytes per step); PLB_FP32 / PLB_FP16S with even nx only, not in
+                                batches [PLB_STREAM_AA].  Both give the same populations. */
 } plb_opts;
+
+enum { PLB_STREAM_AA = 0, PLB_STREAM_FUSED = 1 };
 
 typedef struct plb_state plb_t;
 

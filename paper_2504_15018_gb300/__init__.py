@@ -28,6 +28,7 @@ PLB_D2Q9, PLB_D3Q19 = 0, 1
 PLB_EOS_PR, PLB_EOS_PAPER = 0, 1
 PLB_FP64, PLB_FP32, PLB_FP16S = 0, 1, 2
 PLB_BGK, PLB_MRT = 0, 1
+PLB_STREAM_AA, PLB_STREAM_FUSED = 0, 1
 PLB_MASS, PLB_MOMENTUM, PLB_UMAX, PLB_UL1, PLB_UL2, PLB_MEAN_RHO, PLB_MEAN_P = range(7)
 
 STATUS_NAMES = {0: "PLB_OK", 1: "PLB_EINVAL", 2: "PLB_ENOMEM", 3: "PLB_ECUDA", 4: "PLB_ENONFINITE",
@@ -55,7 +56,7 @@ class plb_opts(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
                 ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double),
                 ("precision", ctypes.c_int), ("rho_ref", ctypes.c_double), ("wall_y", ctypes.c_int),
-                ("body_force", ctypes.c_double * 3), ("fp16_rounding", ctypes.c_int)]
+                ("body_force", ctypes.c_double * 3), ("fp16_rounding", ctypes.c_int), ("streaming", ctypes.c_int)]
 
 
 class plb_instance(ctypes.Structure):

@@ -179,6 +179,9 @@ int plb_batch_create(int lattice, int n, const plb_instance *inst, void *dev_wor
     for (int k = 1; k < n; ++k)
         if (inst[k].opts.precision != inst[0].opts.precision || inst[k].opts.collision != inst[0].opts.collision)
             return plb::set_error(PLB_EINVAL, "all instances of a batch need the same precision and collision");
+    for (int k = 0; k < n; ++k)
+        if (inst[k].opts.streaming != PLB_STREAM_AA)
+            return plb::set_error(PLB_EINVAL, "batches step in place (PLB_STREAM_AA)");
     ArenaLayout A;
     if (!arena_layout(lattice, n, inst, A)) return plb::set_error(PLB_EINVAL, "bad lattice, dims or precision");
     if (!dev_workspace || reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0)

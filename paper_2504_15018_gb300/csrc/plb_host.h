@@ -25,10 +25,11 @@ struct Layout {
     long long psi_elems;
     long long chunk;        // cells per staging chunk
     int max_blocks;         // reduction partial blocks
-    size_t off_pops, off_psi, off_partials, off_out, off_staging, off_flags, total;
+    size_t off_pops, off_pops2, off_psi, off_partials, off_out, off_staging, off_flags, total;
 };
 
-bool make_layout(int lattice, const int dims[3], int precision, Layout &L);
+// streaming = PLB_STREAM_FUSED adds the second population copy (off_pops2; else off_pops2 = off_pops).
+bool make_layout(int lattice, const int dims[3], int precision, Layout &L, int streaming = PLB_STREAM_AA);
 
 struct KParams;
 struct Launchers;
@@ -60,7 +61,8 @@ struct plb_state {
     plb::KParams kp;
     const plb::Launchers *L;
     char *ws;
-    char *pops, *psi;          // population store, padded psi field
+    char *pops, *psi;          // population store (the current copy), padded psi field
+    char *pops2;               // PLB_STREAM_FUSED: the copy the next step writes (else NULL)
     double *partials, *out;    // reduction partials (lay.max_blocks x 4), final values (4)
     double *staging;           // host<->device staging (lay.chunk cells)
     cudaStream_t stream;

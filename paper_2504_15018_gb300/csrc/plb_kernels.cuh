@@ -7,6 +7,7 @@
 #include "plb_device.cuh"
 #include "plb_launch.h"
 #include "plb_batch.cuh"
+#include "plb_fused.cuh"
 #include "plb_pair.cuh"
 #include "plb_step.cuh"
 
@@ -313,11 +314,39 @@ template <class L, class S> struct Launch {
     static void rebalance(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         k_rebalance<L, S><<<blocks(p.n, 256), 256, 0, st>>>(p, (S *)A, (const PsiT *)psi);
     }
+    // single pass: tiles of 64 x 16 cells, each block walking a chunk of zc planes; zc gives
+    // about 1200 blocks (four waves of two blocks on 152 SMs), at least 4 planes per chunk
+    template <int MRT> static void fused_t(const KParams &p, const void *A, void *B, cudaStream_t st) {
+        if constexpr (!std::is_same<S, double>::value) {
+            using Tl = FusedTile<L>;
+            const int gx = (p.nx + Tl::TX - 1) / Tl::TX, gy = (p.ny + Tl::TY - 1) / Tl::TY;
+            int zc = 1, gz = 1;
+            if (L::D == 3) {
+                const long long want = (1200 + (long long)gx * gy - 1) / ((long long)gx * gy);
+                zc = (int)((p.nz + want - 1) / want);
+                if (zc < 4) zc = 4;
+                if (zc > p.nz) zc = p.nz;
+                gz = (p.nz + zc - 1) / zc;
+            }
+            const dim3 grid(gx, gy, gz), block(Tl::THREADS);
+            if constexpr (Store<S>::SHIFT) {
+                if (p.stochastic) {
+                    k_fused_pair<L, S, MRT, true><<<grid, block, 0, st>>>(p, planes(p, A), planes(p, B), zc);
+                    return;
+                }
+            }
+            k_fused_pair<L, S, MRT, false><<<grid, block, 0, st>>>(p, planes(p, A), planes(p, B), zc);
+        }
+    }
+    static void fused_bgk(const KParams &p, const void *A, void *B, cudaStream_t st) { fused_t<0>(p, A, B, st); }
+    static void fused_mrt(const KParams &p, const void *A, void *B, cudaStream_t st) { fused_t<1>(p, A, B, st); }
     static const void *batch_bgk() { return reinterpret_cast<const void *>(&k_batch<L, S, 0>); }
     static const void *batch_mrt() { return reinterpret_cast<const void *>(&k_batch<L, S, 1>); }
     static constexpr Launchers table() {
         return Launchers{&init,     &psi,    {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce,
-                         {&batch_bgk, &batch_mrt}, &rebalance};
+                         {&batch_bgk, &batch_mrt}, &rebalance,
+                         {std::is_same<S, double>::value ? nullptr : &fused_bgk,
+                          std::is_same<S, double>::value ? nullptr : &fused_mrt}};
     }
 };
 

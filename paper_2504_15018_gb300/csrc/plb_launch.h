@@ -83,6 +83,8 @@ struct Launchers {
     const void *(*batch_kernel[2])();
     // balanced start: f^eq(rho, u0) -> f^eq(rho, u0 - F / (2 rho)) at even parity (psi of rho given)
     void (*rebalance)(const KParams &, void *A, const void *psi, cudaStream_t);
+    // single-pass step [BGK, MRT]: reads A (natural layout), pushes into B; NULL for FP64
+    void (*fused[2])(const KParams &, const void *A, void *B, cudaStream_t);
 };
 
 // Defined in plb_kern_fp64.cu / plb_kern_fp32.cu / plb_kern_fp16.cu; lattice 0 = D2Q9, 1 = D3Q19.

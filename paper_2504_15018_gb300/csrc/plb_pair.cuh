@@ -139,19 +139,10 @@ __device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A,
     });
 }
 
-// Force densities of the two cells; pc points at psi of cell x0 (an even padded index).
-template <class L, class Pol = LdStream>
-__device__ __forceinline__ void force_pair(const KParams &p, const float *__restrict__ pc, f2 F[3]) {
-    auto ldg2 = [](const float *a) { return Pol::ro(reinterpret_cast<const float2 *>(a)); };
-    const int sy = p.px, sz = p.px * p.py;
-    // psi of both cells at offset (cx, cy, cz), from three float2 per row
-    auto at = [&](int cx, int cy, int cz) -> f2 {
-        const float *r = pc + cy * sy + cz * sz;
-        const float2 c = ldg2(r);
-        if (cx == 0) return f2(c);
-        if (cx < 0) return f2(ldg2(r - 2).y, c.x);
-        return f2(c.y, ldg2(r + 2).x);
-    };
+// Force densities of the two cells from their psi stencil; at(cx, cy, cz) returns psi of both
+// cells at offset (cx, cy, cz) (the global or the shared-memory psi field).
+template <class L, class At>
+__device__ __forceinline__ void force_pair_from(const KParams &p, At &&at, f2 F[3]) {
     const f2 psi0 = at(0, 0, 0);
     const f2 two_psi0 = psi0 + psi0;
     f2 m1[3] = {f2(0), f2(0), f2(0)};
@@ -186,6 +177,22 @@ __device__ __forceinline__ void force_pair(const KParams &p, const float *__rest
         F[a] = mad(cM, m1[a], mad(cA, m21, f2(q.fext[a])));
     }
     if (L::D == 2) F[2] = f2(0);
+}
+
+// Force densities of the two cells; pc points at psi of cell x0 (an even padded index).
+template <class L, class Pol = LdStream>
+__device__ __forceinline__ void force_pair(const KParams &p, const float *__restrict__ pc, f2 F[3]) {
+    auto ldg2 = [](const float *a) { return Pol::ro(reinterpret_cast<const float2 *>(a)); };
+    const int sy = p.px, sz = p.px * p.py;
+    // psi of both cells at offset (cx, cy, cz), from three float2 per row
+    auto at = [&](int cx, int cy, int cz) -> f2 {
+        const float *r = pc + cy * sy + cz * sz;
+        const float2 c = ldg2(r);
+        if (cx == 0) return f2(c);
+        if (cx < 0) return f2(ldg2(r - 2).y, c.x);
+        return f2(c.y, ldg2(r + 2).x);
+    };
+    force_pair_from<L>(p, at, F);
 }
 
 // psi of one cell into the ghost layer (boundary cells only).

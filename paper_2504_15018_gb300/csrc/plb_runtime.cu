@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "plb.h"
@@ -46,7 +47,7 @@ constexpr unsigned MAGIC = 0x504c4231u;   // "PLB1"
 
 namespace plb {
 
-bool make_layout(int lattice, const int dims[3], int precision, Layout &L) {
+bool make_layout(int lattice, const int dims[3], int precision, Layout &L, int streaming) {
     if (lattice != PLB_D2Q9 && lattice != PLB_D3Q19) return false;
     if (precision < PLB_FP64 || precision > PLB_FP16S) return false;
     if (!dims || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return false;
@@ -68,6 +69,11 @@ bool make_layout(int lattice, const int dims[3], int precision, Layout &L) {
     size_t off = 0;
     L.off_pops = off;
     off = align256(off + (size_t)L.Q * L.pstride * L.s_pop);
+    L.off_pops2 = L.off_pops;
+    if (streaming == PLB_STREAM_FUSED) {
+        L.off_pops2 = off;
+        off = align256(off + (size_t)L.Q * L.pstride * L.s_pop);
+    }
     L.off_psi = off;
     off = align256(off + (size_t)L.psi_elems * L.s_psi);
     L.off_partials = off;
@@ -157,7 +163,7 @@ size_t plb_workspace_bytes(int lattice, const int dims[3], const plb_opts *opts)
     plb_default_opts(&o);
     if (opts) o = *opts;
     plb::Layout L;
-    if (!plb::make_layout(lattice, dims, o.precision, L)) return 0;
+    if (!plb::make_layout(lattice, dims, o.precision, L, o.streaming)) return 0;
     return L.total;
 }
 
@@ -188,7 +194,11 @@ int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos,
     if (!eos) return fail(PLB_EINVAL, "eos is NULL");
     plb_default_opts(&o);
     if (opts) o = *opts;
-    if (!make_layout(lattice, dims, o.precision, lay)) return fail(PLB_EINVAL, "bad lattice, dims or precision");
+    if (o.streaming != PLB_STREAM_AA && o.streaming != PLB_STREAM_FUSED) return fail(PLB_EINVAL, "bad streaming");
+    if (!make_layout(lattice, dims, o.precision, lay, o.streaming))
+        return fail(PLB_EINVAL, "bad lattice, dims or precision");
+    if (o.streaming == PLB_STREAM_FUSED && (o.precision == PLB_FP64 || dims[0] % 2 != 0 || lay.n >= (1LL << 31)))
+        return fail(PLB_EUNSUPPORTED, "fused streaming needs FP32 or FP16S storage, even nx and < 2^31 cells");
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(PLB_EINVAL, "tau must be > 1/2");
     if (!(G < 0.0) || !std::isfinite(G)) return fail(PLB_EINVAL, "G must be negative");
     if (!std::isfinite(eps) || !std::isfinite(o.kappa)) return fail(PLB_EINVAL, "eps and kappa must be finite");
@@ -300,6 +310,7 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     h->lay = lay;
     h->ws = static_cast<char *>(dev_workspace);
     h->pops = h->ws + lay.off_pops;
+    h->pops2 = o.streaming == PLB_STREAM_FUSED ? h->ws + lay.off_pops2 : nullptr;
     h->psi = h->ws + lay.off_psi;
     h->partials = reinterpret_cast<double *>(h->ws + lay.off_partials);
     h->out = reinterpret_cast<double *>(h->ws + lay.off_out);
@@ -394,6 +405,16 @@ int plb_step(plb_t *h, int n) {
     if (!h || n < 0) return fail(PLB_EINVAL, "bad argument");
     if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
+    if (h->pops2) {
+        // single pass: read the current copy, push into the other, swap
+        for (int k = 0; k < n; ++k) {
+            h->kp.salt = (unsigned)h->t;
+            h->L->fused[coll](h->kp, h->pops, h->pops2, h->stream);
+            std::swap(h->pops, h->pops2);
+            h->t += 1;
+        }
+        return check_launch();
+    }
     for (int k = 0; k < n; ++k) {
         h->kp.salt = (unsigned)h->t;
         h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
@@ -416,6 +437,15 @@ int plb_step_timed(plb_t *h, int n, double ms[2]) {
     PLB_CUDA(cudaEventRecord(ev[0], h->stream));
     for (int k = 0; k < n; ++k) {
         h->kp.salt = (unsigned)h->t;
+        if (h->pops2) {
+            // one kernel per step: it is reported as the fused pass, the psi interval is empty
+            cudaEventRecord(ev[2 * k + 1], h->stream);
+            h->L->fused[coll](h->kp, h->pops, h->pops2, h->stream);
+            cudaEventRecord(ev[2 * k + 2], h->stream);
+            std::swap(h->pops, h->pops2);
+            h->t += 1;
+            continue;
+        }
         h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
         cudaEventRecord(ev[2 * k + 1], h->stream);
         h->L->collide[coll](h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);

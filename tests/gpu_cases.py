@@ -81,6 +81,8 @@ def make_lattice(case, rv, rl):
         kw.update(rho_ref=case["rho_ref"])
     if case.get("fp16_rounding"):
         kw.update(fp16_rounding=case["fp16_rounding"])
+    if case.get("streaming"):
+        kw.update(streaming=case["streaming"])
     return plb.Lattice(case["lattice"], case["dims"], eos, tau=case.get("tau", 1.0), G=case.get("G", -1.0),
                        eps=case.get("eps", 2.0), opts=plb.make_opts(**kw))
 

@@ -101,6 +101,11 @@ def test_workspace_layout(L):
     o16 = plb.make_opts(precision=plb.PLB_FP16S)
     assert plb.plb_workspace_bytes(plb.PLB_D3Q19, (64, 64, 64), o16) < plb.plb_workspace_bytes(
         plb.PLB_D3Q19, (64, 64, 64), o)
+    # single-pass stepping keeps a second population copy (planes padded to 128 cells)
+    of = plb.make_opts(precision=plb.PLB_FP32, streaming=plb.PLB_STREAM_FUSED)
+    assert plb.plb_workspace_bytes(plb.PLB_D3Q19, (512, 256, 256), of) == n + pops
+    assert plb.plb_workspace_bytes(plb.PLB_D2Q9, (30, 7, 1), of) - plb.plb_workspace_bytes(
+        plb.PLB_D2Q9, (30, 7, 1), o) == (9 * 256 * 4 + 255) // 256 * 256
 
 
 def test_create_rejects_bad_arguments_without_touching_the_device(L):

@@ -179,3 +179,76 @@ def test_batch_init_physical_matches_a_single_lattice():
         lat.init(rho, u0, physical=True)
         lat.step(5)
         assert np.array_equal(b.populations(k), lat.populations()), k
+
+
+def _batch96():
+    """The 96 uneven D2Q9 instances of the batched workload (FP32, MRT, tau = 1), as bench.py
+    builds them."""
+    import paper_2504_15018_gb300 as plb
+    desc = inputs.batched_d2q9_instances(96)
+    insts, fields = [], []
+    for d in desc:
+        side = d["side"]
+        eos = plb.pr_eos(d["T_over_Tc"])
+        rv, rl, _ = plb.plb_solve_params(eos)
+        opts = plb.make_opts(precision=plb.PLB_FP32, collision=plb.PLB_MRT, s_e=1.19, s_eps=1.4, s_q=1.2,
+                             s_pi=1.4, s_m=1.98)
+        insts.append(plb.make_instance((side, side, 1), eos, tau=1.0, opts=opts))
+        dims = (side, side, 1)
+        u0 = None
+        if d["kind"] == "planar":
+            rho = inputs.slab(dims, 1, side // 4, 3 * side // 4, rl, rv, 4.0)
+        else:
+            rho = inputs.droplet(dims, (side / 2, side / 2), d["radius"], rv, rl, 4.0)
+            if d["kind"] == "translating":
+                u0 = np.zeros((2, side * side))
+                u0[0], u0[1] = d["velocity"]
+        fields.append((rho, u0))
+    return desc, insts, fields
+
+
+def _centroid(rho, side, floor):
+    """Periodic (circular-mean) centroid of the density above floor, per axis."""
+    m = np.clip(rho.reshape(side, side) - floor, 0.0, None)
+    ang = 2 * np.pi * np.arange(side) / side
+    out = []
+    for w in (m.sum(axis=0), m.sum(axis=1)):            # x then y
+        out.append(np.arctan2((w * np.sin(ang)).sum(), (w * np.cos(ang)).sum()) * side / (2 * np.pi))
+    return np.array(out)
+
+
+def test_batch96_workload_matches_lone_instances_and_translates_droplets():
+    """The full 96-instance workload in one batch, 1000 steps: the smallest and largest
+    instances and one of each kind evolve bit for bit as when stepped alone, and every
+    translating droplet's centroid moves by U t (within 2 % of the distance travelled plus a
+    quarter cell: the Galilean error of the interface)."""
+    import paper_2504_15018_gb300 as plb
+    desc, insts, fields = _batch96()
+    b = plb.Batch(plb.PLB_D2Q9, insts)
+    for k, (rho, u0) in enumerate(fields):
+        b.init(k, rho, u0)
+    b.configure(tile_cells=1024)
+    steps = 1000
+    b.step(steps)
+    b.status()
+    sides = [d["side"] for d in desc]
+    sample = {int(np.argmin(sides)), int(np.argmax(sides))}
+    for kind in ("static", "translating", "planar"):
+        sample.add(next(k for k, d in enumerate(desc) if d["kind"] == kind))
+    for k in sorted(sample):
+        assert np.array_equal(b.populations(k), _alone(0, insts[k], *fields[k], steps)), k
+    checked = 0
+    for k, d in enumerate(desc):
+        if d["kind"] != "translating" or d["radius"] < 10:
+            continue
+        side = d["side"]
+        rv, rl, _ = plb.plb_solve_params(insts[k].eos)
+        floor = 0.5 * (rv + rl)
+        c0 = _centroid(fields[k][0], side, floor)
+        rho = b.moments(k)[0]
+        c1 = _centroid(rho, side, floor)
+        want = np.array(d["velocity"]) * steps
+        err = np.abs((c1 - c0 - want + side / 2) % side - side / 2).max()
+        assert err < 0.02 * np.abs(want).max() + 0.25, (k, c1 - c0, want)
+        checked += 1
+    assert checked >= 3

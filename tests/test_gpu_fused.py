@@ -1,0 +1,88 @@
+"""Single-pass stepping (PLB_STREAM_FUSED): psi of each tile and its halo formed in shared
+memory, force, collision and push streaming in one kernel, two population copies.  The
+per-cell arithmetic is the code of the two-pass in-place (AA) kernels, so after any number of
+steps both give the same populations bit for bit; ragged tiles (nx, ny not multiples of the
+64 x 16 tile, nz not a multiple of the z chunk), walls, one-row and two-column lattices, BGK
+and MRT, FP32, FP16S and FP16S with stochastic rounding are covered.  Readouts, state and
+the balanced start work on the current copy."""
+import numpy as np
+import pytest
+
+from gpu_cases import case_fields, make_lattice
+
+pytestmark = pytest.mark.gpu
+
+RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.3, s_m=1.5)
+CASES = {
+    "d3q19_fp32_mrt_walls_ragged": dict(lattice=1, dims=(70, 20, 9), wall=True, shape="slab", mrt=True, rates=RATES,
+                                        fext=(2e-6, 0, 0), precision=1),
+    "d3q19_fp32_bgk_zchunks": dict(lattice=1, dims=(64, 48, 40), u0=(0.02, -0.01, 0.015), precision=1),
+    "d3q19_fp32_mrt_one_plane": dict(lattice=1, dims=(18, 10, 1), mrt=True, rates=RATES, precision=1),
+    "d2q9_fp32_bgk_droplet": dict(lattice=0, dims=(130, 67, 1), precision=1),
+    "d2q9_fp32_mrt_walls_taurho": dict(lattice=0, dims=(96, 20, 1), wall=True, shape="slab", mrt=True, rates=RATES,
+                                       tau=0.8, tau_v=1.1, fext=(1e-5, 0, 0), precision=1),
+    "d2q9_fp32_two_wide": dict(lattice=0, dims=(2, 40, 1), shape="slab", precision=1),
+    "d2q9_fp32_one_row": dict(lattice=0, dims=(66, 1, 1), shape="slab", precision=1),
+    "d3q19_fp16s_mrt_walls": dict(lattice=1, dims=(34, 18, 12), wall=True, shape="slab", mrt=True, rates=RATES,
+                                  precision=2),
+    "d3q19_fp16s_sr_mrt_walls": dict(lattice=1, dims=(34, 18, 12), wall=True, shape="slab", mrt=True, rates=RATES,
+                                     precision=2, fp16_rounding=1),
+    "d2q9_fp16s_bgk_droplet": dict(lattice=0, dims=(80, 70, 1), precision=2),
+}
+
+
+def _pair(name, steps, physical=False):
+    case = CASES[name]
+    rho, u0, rv, rl = case_fields(case)
+    out = []
+    for streaming in (0, 1):
+        lat = make_lattice(dict(case, streaming=streaming), rv, rl)
+        lat.init(rho, u0, physical=physical)
+        lat.step(steps)
+        lat.status()
+        out.append(lat)
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fused_matches_the_two_pass_kernels_bit_for_bit(name):
+    aa, fu = _pair(name, 7)
+    assert np.array_equal(aa.populations(), fu.populations())
+    aa.step(6)
+    fu.step(6)
+    assert np.array_equal(aa.populations(), fu.populations())
+    assert fu.time == 13
+
+
+def test_fused_readouts_state_and_balanced_start():
+    import paper_2504_15018_gb300 as plb
+    aa, fu = _pair("d3q19_fp32_mrt_walls_ragged", 5, physical=True)
+    for a, b in zip(aa.moments(), fu.moments()):
+        assert np.array_equal(a, b)
+    for what in (plb.PLB_MASS, plb.PLB_MOMENTUM, plb.PLB_UMAX, plb.PLB_UL2):
+        assert np.array_equal(aa.reduce(what), fu.reduce(what))
+    assert np.array_equal(aa.reduce(plb.PLB_MEAN_P, (2, 3, 1), (9, 11, 5)), fu.reduce(plb.PLB_MEAN_P, (2, 3, 1), (9, 11, 5)))
+    st = fu.get_state()
+    fu.step(4)
+    f4 = fu.populations()
+    fu.set_state(st)
+    fu.step(4)
+    assert np.array_equal(fu.populations(), f4)
+    f = fu.populations()
+    fu.set_populations(f)
+    assert np.array_equal(fu.populations(), f)
+
+
+def test_fused_needs_fp32_arithmetic_even_nx_and_no_batch():
+    import paper_2504_15018_gb300 as plb
+    from gpu_cases import maxwell
+    rv, rl, _ = maxwell(0.8)
+    for prec, dims in ((0, (16, 8, 4)), (1, (15, 8, 4))):
+        o = plb.make_opts(precision=prec, streaming=plb.PLB_STREAM_FUSED)
+        with pytest.raises(plb.PlbError) as e:
+            plb.Lattice(plb.PLB_D3Q19, dims, plb.pr_eos(0.8), opts=o)
+        assert e.value.code == plb.PLB_EUNSUPPORTED
+    o = plb.make_opts(precision=1, streaming=plb.PLB_STREAM_FUSED)
+    with pytest.raises(plb.PlbError) as e:
+        plb.Batch(plb.PLB_D2Q9, [plb.make_instance((16, 16, 1), plb.pr_eos(0.8), opts=o)])
+    assert e.value.code == plb.PLB_EINVAL

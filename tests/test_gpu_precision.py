@@ -40,15 +40,19 @@ def pr_eos_pressure(rho, t_ratio):
     return float(pp.pr_pressure(rho, a, b, 1.0, om, t_ratio * pp.pr_Tc(a, b)))
 
 
-def _laplace(precision, t_ratio=0.8, radii=(20, 30, 40, 50, 60), n=256, steps=40000, stochastic=0):
+def _laplace(precision, t_ratios=(0.8,), radii=(20, 30, 40, 50, 60), n=256, steps=40000, stochastic=0):
+    """Static droplets of radius R0 at the centre of a periodic n x n box for every T/Tc, all in
+    one batch.  Returns {T/Tc: (gamma, rows)}, rows = (R, Delta P, rho_in, rho_out, max |u|)."""
     import paper_2504_15018_gb300 as plb
-    rv, rl = mech_densities(t_ratio)
-    insts, fields = [], []
-    for R in radii:
-        opts = plb.make_opts(precision=precision, fp16_rounding=stochastic)
-        insts.append(plb.make_instance((n, n, 1), plb.pr_eos(t_ratio), tau=1.0, opts=opts))
-        fields.append(inputs.laplace_d2q9_256(rv, rl, R)[1] if n == 256 else
-                      inputs.droplet((n, n, 1), (n / 2, n / 2), R, rv, rl, 4.0))
+    insts, fields, keys = [], [], []
+    for t_ratio in t_ratios:
+        rv, rl = mech_densities(t_ratio)
+        for R in radii:
+            opts = plb.make_opts(precision=precision, fp16_rounding=stochastic)
+            insts.append(plb.make_instance((n, n, 1), plb.pr_eos(t_ratio), tau=1.0, opts=opts))
+            fields.append(inputs.laplace_d2q9_256(rv, rl, R)[1] if n == 256 else
+                          inputs.droplet((n, n, 1), (n / 2, n / 2), R, rv, rl, 4.0))
+            keys.append((t_ratio, R))
     b = plb.Batch(plb.PLB_D2Q9, insts)
     for k, rho in enumerate(fields):
         b.init(k, rho)
@@ -58,35 +62,46 @@ def _laplace(precision, t_ratio=0.8, radii=(20, 30, 40, 50, 60), n=256, steps=40
     # time average of 40 snapshots, 250 steps apart, over a centred square of half-width
     # 0.35 R0 and a 32 x 32 corner square: the liquid branch of the EOS is steep (Delta P to 1 %
     # needs rho_in to ~1e-5), and FP16 storage adds per-step noise to rho
-    acc = np.zeros((len(radii), 4))
+    acc = np.zeros((len(insts), 4))
     nsnap = 40
     for _ in range(nsnap):
         b.step(250)
-        for k in range(len(radii)):
-            h = max(4, int(0.35 * radii[k]))
+        for k, (_, R0) in enumerate(keys):
+            h = max(4, int(0.35 * R0))
             acc[k] += (b.reduce(k, plb.PLB_MASS)[0],
                        b.reduce(k, plb.PLB_MEAN_RHO, (c - h, c - h, 0), (c + h + 1, c + h + 1, 1))[0],
                        b.reduce(k, plb.PLB_MEAN_RHO, (0, 0, 0), (32, 32, 1))[0],
                        b.reduce(k, plb.PLB_UMAX)[0])
+    b.status()
     acc /= nsnap
-    rows = []
-    for k in range(len(radii)):
-        mass, r_in, r_out, umax = acc[k]
-        p_in, p_out = pr_eos_pressure(r_in, t_ratio), pr_eos_pressure(r_out, t_ratio)
-        R = math.sqrt(max(mass - r_out * n * n, 0.0) / (math.pi * max(r_in - r_out, 1e-30)))
-        print(f"precision {precision} sr {stochastic} R0 {radii[k]}: R {R:.3f} dP {p_in - p_out:.6e} "
-              f"rho_in {r_in:.6f} rho_out {r_out:.6f} umax {umax:.3e}")
-        rows.append((R, p_in - p_out, r_in, r_out, umax))
-    rows = np.array(rows)
-    A = np.stack([1.0 / rows[:, 0], np.ones(len(rows))], axis=1)
-    gamma, c0 = np.linalg.lstsq(A, rows[:, 1], rcond=None)[0]
-    return gamma, rows
+    out = {}
+    for t_ratio in t_ratios:
+        rv, rl = mech_densities(t_ratio)
+        rows = []
+        for k, (t, R0) in enumerate(keys):
+            if t != t_ratio:
+                continue
+            mass, r_in, r_out, umax = acc[k]
+            p_in, p_out = pr_eos_pressure(r_in, t_ratio), pr_eos_pressure(r_out, t_ratio)
+            R = math.sqrt(max(mass - r_out * n * n, 0.0) / (math.pi * max(r_in - r_out, 1e-30)))
+            alive = r_in - r_out > 0.5 * (rl - rv)
+            print(f"precision {precision} sr {stochastic} T/Tc {t_ratio} R0 {R0}: R {R:.3f} dP {p_in - p_out:.6e} "
+                  f"rho_in {r_in:.6f} rho_out {r_out:.6f} umax {umax:.3e}" + ("" if alive else " (evaporated)"))
+            if alive:      # a droplet below the critical radius evaporates into the supersaturated vapour
+                rows.append((R, p_in - p_out, r_in, r_out, umax))
+        rows = np.array(rows)
+        A = np.stack([1.0 / rows[:, 0], np.ones(len(rows))], axis=1)
+        gamma, c0 = np.linalg.lstsq(A, rows[:, 1], rcond=None)[0]
+        out[t_ratio] = (gamma, rows)
+    return out
 
 
 @pytest.fixture(scope="module")
 def laplace_runs():
+    """T/Tc = 0.7, 0.8, 0.9 x R0 = 20 ... 60 in FP64 and FP32; T/Tc = 0.8 in FP16S."""
     import paper_2504_15018_gb300 as plb
-    runs = {"fp64": _laplace(plb.PLB_FP64), "fp32": _laplace(plb.PLB_FP32),
+    temps = (0.7, 0.8, 0.9)
+    runs = {"fp64": _laplace(plb.PLB_FP64, temps), "fp32": _laplace(plb.PLB_FP32, temps),
             "fp16s_sr": _laplace(plb.PLB_FP16S, stochastic=1)}
     try:
         runs["fp16s_rne"] = _laplace(plb.PLB_FP16S)
@@ -96,30 +111,46 @@ def laplace_runs():
 
 
 def test_laplace_surface_tension_matches_fp64(laplace_runs):
-    """FP32 and FP16S with stochastic rounding hold the surface tension within 1 % of FP64.
-    FP16S with round-to-nearest does not: its stores stop changing once the per-step update is
-    below half an FP16 ulp (stagnation), freezing the droplets before they relax, and the
-    repeated rounding of near-steady values biases the mass (reported, not asserted)."""
-    g64, rows64 = laplace_runs["fp64"]
-    assert 0.05 < g64 < 0.2                 # diffusive-limit value 0.1023 (App. A/B for the PR EOS)
-    # Laplace's law itself: the fit explains Delta P
-    resid = rows64[:, 1] - (g64 / rows64[:, 0] + np.mean(rows64[:, 1] - g64 / rows64[:, 0]))
-    assert np.max(np.abs(resid)) < 0.05 * np.max(np.abs(rows64[:, 1]))
-    for name in ("fp32", "fp16s_sr"):
-        g, rows = laplace_runs[name]
-        print(f"{name}: gamma {g:.6f} vs fp64 {g64:.6f} ({(g / g64 - 1) * 100:+.3f} %)")
-        assert abs(g / g64 - 1) < 0.01
+    """FP32 (T/Tc = 0.7, 0.8, 0.9) and FP16S with stochastic rounding (0.8) hold the surface
+    tension within 1 % of FP64.  At T/Tc = 0.9 the R0 = 20 droplet is below the critical radius
+    and evaporates; it is left out of the fit (in every precision).  FP16S with round-to-nearest does not: its stores stop changing
+    once the per-step update is below half an FP16 ulp (stagnation), freezing the droplets
+    before they relax, and the repeated rounding of near-steady values biases the mass
+    (reported, not asserted).  The FP64 gamma is reported beside the diffusive-limit value of
+    App. A/B applied to the PR EOS (kappa = 1); at p_scale = 1 the interface is 1-2 cells wide,
+    so the gap is the O(dx^2) error of the coarse interface, not a failure."""
+    from oracle import params as pp
+    a, b_, om = 2 / 49, 2 / 21, 0.327
+    for t_ratio, (g64, rows64) in laplace_runs["fp64"].items():
+        assert len(rows64) >= 4            # at most the smallest droplet evaporates (T/Tc = 0.9)
+        T = t_ratio * pp.pr_Tc(a, b_)
+        rv, rl, p0 = pp.pr_maxwell(a, b_, 1.0, om, T)
+        g_lim = pp.diffusive_gamma(lambda r: pp.pr_pressure(r, a, b_, 1.0, om, T), rv, rl, p0)
+        print(f"T/Tc {t_ratio}: fp64 gamma {g64:.6f} (diffusive limit {g_lim:.6f}); spurious max|u| "
+              f"{rows64[:, 4].max():.3e}")
+        assert 0.3 * g_lim < g64 < 3 * g_lim
+        # Laplace's law itself: the fit explains Delta P
+        resid = rows64[:, 1] - (g64 / rows64[:, 0] + np.mean(rows64[:, 1] - g64 / rows64[:, 0]))
+        assert np.max(np.abs(resid)) < 0.05 * np.max(np.abs(rows64[:, 1]))
+        for name in ("fp32", "fp16s_sr"):
+            if t_ratio not in laplace_runs[name]:
+                continue
+            g, rows = laplace_runs[name][t_ratio]
+            print(f"  {name}: gamma {g:.6f} vs fp64 {g64:.6f} ({(g / g64 - 1) * 100:+.3f} %)")
+            assert abs(g / g64 - 1) < 0.01
     rne = laplace_runs["fp16s_rne"]
+    g64 = laplace_runs["fp64"][0.8][0]
     print("fp16s round-to-nearest:", "no fit (a droplet evaporated)" if rne is None else
-          f"gamma {rne[0]:.6f} ({(rne[0] / g64 - 1) * 100:+.2f} %)")
+          f"gamma {rne[0.8][0]:.6f} ({(rne[0.8][0] / g64 - 1) * 100:+.2f} %)")
 
 
 def test_droplet_coexistence_densities_match_fp64(laplace_runs):
-    _, rows64 = laplace_runs["fp64"]
     for name in ("fp32", "fp16s_sr"):
-        _, rows = laplace_runs[name]
-        assert np.max(np.abs(rows[:, 2] / rows64[:, 2] - 1)) < 0.005   # liquid
-        assert np.max(np.abs(rows[:, 3] / rows64[:, 3] - 1)) < 0.005   # vapour
+        for t_ratio, (_, rows) in laplace_runs[name].items():
+            rows64 = laplace_runs["fp64"][t_ratio][1]
+            assert len(rows) == len(rows64)
+            assert np.max(np.abs(rows[:, 2] / rows64[:, 2] - 1)) < 0.005   # liquid
+            assert np.max(np.abs(rows[:, 3] / rows64[:, 3] - 1)) < 0.005   # vapour
 
 
 def _planar(precision, steps=20000, stochastic=0):
@@ -168,7 +199,7 @@ def test_planar_coexistence_8x256_all_precisions():
     assert abs(v64 - mv) < abs(v64 - rv)
 
 
-def _ladder(precision, levels, n0=64, steps0=1000):
+def _ladder(precision, levels, n0=64, steps0=1000, stochastic=0):
     import paper_2504_15018_gb300 as plb
     rv, rl, _ = maxwell(0.8)
     out = []
@@ -177,7 +208,7 @@ def _ladder(precision, levels, n0=64, steps0=1000):
         eos = plb.pr_eos(0.8, p_scale=4.0 ** -k)
         dims, rho = inputs.droplet_d3q19(n, rv, rl, width=4.0 * 2 ** k)
         lat = plb.Lattice(plb.PLB_D3Q19, dims, eos, 1.0, -1.0, 2.0,
-                          opts=plb.make_opts(precision=precision, collision=plb.PLB_MRT,
+                          opts=plb.make_opts(precision=precision, collision=plb.PLB_MRT, fp16_rounding=stochastic,
                                              s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98))
         lat.init(rho)
         lat.step(steps0 * 4 ** k)
@@ -196,7 +227,9 @@ def test_diffusive_refinement_converges_second_order():
     """D3Q19 droplet, R = N/4, N = 64, 128, 256 with Delta t ~ Delta x^2 (p_EOS x 4^-k, steps
     1000 x 4^k, tanh width 4 x 2^k); MRT; FP32 storage.  Differences between successive levels
     approach second order (observed order rises with resolution).  FP64 at N = 64 and 128
-    agrees with FP32 to 5e-4 (relative L2 of a transient)."""
+    agrees with FP32 to 5e-4 (relative L2 of a transient).  FP16S with stochastic rounding on
+    the same ladder: its order and its distance from FP64 are reported (the FP16 noise,
+    ~2^-11 of w_i rho_l per store, is below the level differences)."""
     import paper_2504_15018_gb300 as plb
     r32 = _ladder(plb.PLB_FP32, (0, 1, 2))
     e = [np.sqrt(np.mean((r32[k] - _restrict(r32[k + 1])) ** 2)) / np.sqrt(np.mean(r32[k] ** 2)) for k in range(2)]
@@ -211,6 +244,13 @@ def test_diffusive_refinement_converges_second_order():
         assert d < 5e-4
     # measured 1.66 on 64 / 128 / 256 (1.42 on 32 / 64 / 128): approaching 2 from below
     assert order > 1.5
+    r16 = _ladder(plb.PLB_FP16S, (0, 1, 2), stochastic=1)
+    e16 = [np.sqrt(np.mean((r16[k] - _restrict(r16[k + 1])) ** 2)) / np.sqrt(np.mean(r16[k] ** 2)) for k in range(2)]
+    d16 = [np.sqrt(np.mean((r16[k] - r64[k]) ** 2)) / np.sqrt(np.mean(r64[k] ** 2)) for k in range(2)]
+    print(f"fp16s-sr: level differences {e16[0]:.4e} {e16[1]:.4e}, observed order {math.log2(e16[0] / e16[1]):.3f}; "
+          f"relative L2 vs fp64 at N = 64, 128: {d16[0]:.3e} {d16[1]:.3e}")
+    assert math.log2(e16[0] / e16[1]) > 1.4
+    assert max(d16) < 0.1 * e[1]
 
 
 MRT_RATES = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98)
