@@ -108,6 +108,11 @@ typedef struct plb_opts {
                                 the populations (twice the population memory, about 30 % fewer DRAM
                                 bytes per step); PLB_FP32 / PLB_FP16S with even nx only, not in
                                 batches [PLB_STREAM_AA].  Both give the same populations. */
+    double wall_rho;         /* wall_y = 1 only: > 0 makes the walls wetting walls, whose nodes carry
+                                the pseudo-potential psi(wall_rho) of a prescribed wall density
+                                instead of mirroring the adjacent fluid row; wall_rho near rho_l
+                                wets, near rho_v does not (not in the paper, which has neutral
+                                walls only); <= 0: mirror rule [0] */
 } plb_opts;
 
 enum { PLB_STREAM_AA = 0, PLB_STREAM_FUSED = 1 };

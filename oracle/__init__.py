@@ -18,6 +18,8 @@ Parity status per function (see the tests that pin each one):
     the parabolic Poiseuille profile between bounce-back walls, MRT == BGK when all
     rates equal 1/tau, and planar-interface coexistence at the Maxwell densities.
   - MRT ghost-moment rates: parity unpinned (the paper gives no values).
+  - Wetting walls (wall_rho): not in the paper; pinned by a uniform state at the wall density
+    staying at rest, by the mirror-rule limit and by the order of contact angles.
 """
 from __future__ import annotations
 
@@ -57,6 +59,7 @@ class OrcParams(ctypes.Structure):
         ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double),
         ("fext", ctypes.c_double * 3),
         ("eps_printed", ctypes.c_int),
+        ("wall_rho", ctypes.c_double),
     ]
 
 
@@ -106,12 +109,13 @@ def _dp(a: np.ndarray | None):
 def make_params(lattice: int, dims, *, wall_y: bool = False, eos: dict, G: float = -1.0,
                 eps: float = 2.0, kappa: float = 1.0, tau: float = 1.0, tau_v: float | None = None,
                 tau_rho=(0.0, 1.0), mrt: bool = False, rates=None, fext=(0.0, 0.0, 0.0),
-                p_scale: float = 1.0, eps_printed: bool = False) -> OrcParams:
+                p_scale: float = 1.0, eps_printed: bool = False, wall_rho: float = 0.0) -> OrcParams:
     """Build the C parameter block.
 
     ``eos`` is ``{"kind": "pr", "a", "b", "R", "omega", "T"}`` (absolute T) or
     ``{"kind": "paper", "rho_v", "rho_l", "P"}`` with P = p_c / rho_c^3.
     ``rates`` = dict(s_e, s_eps, s_q, s_pi, s_m) for MRT.
+    ``wall_rho`` > 0: psi on the wall nodes is psi(wall_rho) (wetting walls); 0: mirror rule.
     """
     P = OrcParams()
     P.lattice = lattice
@@ -137,6 +141,7 @@ def make_params(lattice: int, dims, *, wall_y: bool = False, eos: dict, G: float
     for a in range(3):
         P.fext[a] = fext[a]
     P.eps_printed = int(bool(eps_printed))
+    P.wall_rho = wall_rho
     return P
 
 

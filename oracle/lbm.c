@@ -33,6 +33,8 @@
  *     with S = I / tau this is exactly the BGK update with Guo forcing.
  *   - Solid walls are halfway bounce-back at y = -1/2 and y = ny - 1/2; psi on a wall
  *     node equals psi on the fluid node it mirrors (y = -1 <-> 0, y = ny <-> ny - 1).
+ *     With wall_rho > 0 the wall nodes instead carry psi(wall_rho), the pseudo-potential of
+ *     a prescribed wall density (wetting walls: wall_rho near rho_l wets, near rho_v does not).
  *   - The tau interpolation weight is clamped to [0, 1].
  *   - Eq. interactionForce and Eq. New_Pressure_Tensor disagree on the eps term: the
  *     continuum limit of -G/12 (3 eps/2) M1_b M2_ab adds +G/16 eps (d psi)^2 to p_ab,
@@ -70,6 +72,7 @@ typedef struct {
     double fext[3];           /* external body force density */
     int eps_printed;          /* 1: eps coefficient exactly as printed in Eq. interactionForce (3 eps / 2);
                                  0: the reading that realises Eq. New_Pressure_Tensor (-3 eps), see below */
+    double wall_rho;          /* > 0: psi on wall nodes = psi(wall_rho); <= 0: mirror of the fluid row */
 } orc_params;
 
 /* ---------------------------------------------------------------- lattices */
@@ -304,11 +307,17 @@ static long cell_index(const orc_params *P, int x, int y, int z) {
 
 static int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-/* psi at x + c (periodic wrap; walls mirror psi of the adjacent fluid row). */
+/* psi at x + c (periodic wrap; walls mirror psi of the adjacent fluid row, or carry
+   psi(wall_rho) when a wall density is prescribed). */
 static double psi_neighbour(const orc_params *P, const double *psi, int x, int y, int z, const int *c) {
     int xn = wrap(x + c[0], P->nx);
     int zn = wrap(z + c[2], P->nz);
     int yn = y + c[1];
+    if (P->wall_y && P->wall_rho > 0.0 && (yn < 0 || yn >= P->ny)) {
+        double pw = 0.0;
+        psi_of_rho(P, P->wall_rho, &pw);     /* validated in check_params */
+        return pw;
+    }
     if (P->wall_y) {
         if (yn < 0) yn = -1 - yn;
         if (yn >= P->ny) yn = 2 * P->ny - 1 - yn;
@@ -324,6 +333,10 @@ static int check_params(const orc_params *P) {
     if (P->lattice == 0 && P->nz != 1) return ORC_EINVAL;
     if (!(P->G < 0.0)) return ORC_EINVAL;
     if (!(P->tau_l > 0.5) || !(P->tau_v > 0.5)) return ORC_EINVAL;
+    if (P->wall_rho > 0.0) {
+        double pw;
+        if (psi_of_rho(P, P->wall_rho, &pw) != ORC_OK) return ORC_EINVAL;
+    }
     return ORC_OK;
 }
 

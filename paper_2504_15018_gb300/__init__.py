@@ -56,7 +56,8 @@ class plb_opts(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_eps", ctypes.c_double), ("s_q", ctypes.c_double),
                 ("s_pi", ctypes.c_double), ("s_m", ctypes.c_double),
                 ("precision", ctypes.c_int), ("rho_ref", ctypes.c_double), ("wall_y", ctypes.c_int),
-                ("body_force", ctypes.c_double * 3), ("fp16_rounding", ctypes.c_int), ("streaming", ctypes.c_int)]
+                ("body_force", ctypes.c_double * 3), ("fp16_rounding", ctypes.c_int), ("streaming", ctypes.c_int),
+                ("wall_rho", ctypes.c_double)]
 
 
 class plb_instance(ctypes.Structure):

@@ -273,6 +273,10 @@ int plb_batch_create(int lattice, int n, const plb_instance *inst, void *dev_wor
         bi.upr = bi.pair ? inst[k].dims[0] / 2 : inst[k].dims[0];
         e = cudaMemsetAsync(h->psi, 0, (size_t)lay.psi_elems * lay.s_psi, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->kp.flags, 0, 64, b->stream);
+        if (e == cudaSuccess && h->kp.wall_fixed) {
+            b->L->wall_fill(h->kp, h->psi, b->stream);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return fail_destroy(plb::set_error(PLB_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
     }
     e = cudaMemsetAsync(b->ws + A.off_bar, 0, sizeof(plb::GridBar), b->stream);

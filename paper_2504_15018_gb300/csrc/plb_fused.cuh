@@ -38,6 +38,12 @@ __device__ __forceinline__ void fused_psi_plane(const KParams &p, const Planes<S
     for (int k = threadIdx.x; k < Tl::RY * Tl::HP; k += Tl::THREADS) {
         const int ly = k / Tl::HP, hp = k - ly * Tl::HP;
         int y = y0 - 1 + ly;
+        float *dst = plane + ly * (2 * Tl::HP) + 2 * hp;
+        if (p.wall_fixed && (y < 0 || y >= p.ny)) {
+            // wetting walls: the nodes beyond the walls carry psi_wall
+            *reinterpret_cast<float2 *>(dst) = make_float2(p.f.psi_wall, p.f.psi_wall);
+            continue;
+        }
         if (p.wall_y) {
             // the ghost rows beyond the walls mirror the first and last fluid rows; rows past
             // the halo of a ragged tile are clamped (computed, never read)
@@ -57,7 +63,7 @@ __device__ __forceinline__ void fused_psi_plane(const KParams &p, const Planes<S
         for (int i = 1; i < L::Q; ++i) rho += f[i];
         if (Store<S>::SHIFT) rho += f2(p.f.rho_ref);   // sum_i w_i rho_ref = rho_ref
         const f2 v = psi_pair_of(p, rho);
-        *reinterpret_cast<float2 *>(plane + ly * (2 * Tl::HP) + 2 * hp) = v.v;
+        *reinterpret_cast<float2 *>(dst) = v.v;
     }
 }
 

@@ -118,6 +118,23 @@ __global__ void k_rebalance(KParams p, S *__restrict__ A, const typename Store<S
     });
 }
 
+// ------------------------------------------------------------- wetting walls
+// psi_wall into the ghost rows y = -1 and y = ny of the padded psi field, over the ghost columns
+// and planes too (every node beyond a wall).  Nothing else writes these rows when the walls
+// are wetting (psi_ghosts skips them), so this runs once, when the lattice is created.
+template <class L, class S>
+__global__ void k_wall_fill(KParams p, typename Store<S>::PsiT *__restrict__ psi) {
+    using T = typename Store<S>::T;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long cols = (long long)p.nx + 2, planes = L::D == 3 ? p.nz + 2 : 1;
+    if (k >= cols * planes) return;
+    const int x = (int)(k % cols) - 1;
+    const int z = L::D == 3 ? (int)(k / cols) - 1 : 0;
+    const typename Store<S>::PsiT v = (typename Store<S>::PsiT)phys<T>(p).psi_wall;
+    psi[psi_index(p, x, -1, z)] = v;
+    psi[psi_index(p, x, p.ny, z)] = v;
+}
+
 // ------------------------------------------------------ population exchange
 template <class L, class S>
 __global__ void k_get_pops(KParams p, const S *__restrict__ A, int odd, double *__restrict__ out, long long c0,
@@ -311,6 +328,10 @@ template <class L, class S> struct Launch {
         k_reduce<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, what, lo[0], lo[1], lo[2],
                                                 hi[0], hi[1], hi[2], partials);
     }
+    static void wall_fill(const KParams &p, void *psi, cudaStream_t st) {
+        const long long n = ((long long)p.nx + 2) * (L::D == 3 ? p.nz + 2 : 1);
+        k_wall_fill<L, S><<<blocks(n, 256), 256, 0, st>>>(p, (PsiT *)psi);
+    }
     static void rebalance(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         k_rebalance<L, S><<<blocks(p.n, 256), 256, 0, st>>>(p, (S *)A, (const PsiT *)psi);
     }
@@ -344,7 +365,7 @@ template <class L, class S> struct Launch {
     static const void *batch_mrt() { return reinterpret_cast<const void *>(&k_batch<L, S, 1>); }
     static constexpr Launchers table() {
         return Launchers{&init,     &psi,    {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce,
-                         {&batch_bgk, &batch_mrt}, &rebalance,
+                         {&batch_bgk, &batch_mrt}, &rebalance, &wall_fill,
                          {std::is_same<S, double>::value ? nullptr : &fused_bgk,
                           std::is_same<S, double>::value ? nullptr : &fused_mrt}};
     }

@@ -20,6 +20,7 @@ template <class T> struct Phys {
     T pr_RT, pr_b, pr_aalpha;
     T pe_P, pe_rv, pe_rl, pe_sv;
     T p_scale;
+    T psi_wall;               // psi on wetting walls (used when KParams::wall_fixed)
 };
 
 struct KParams {
@@ -27,6 +28,7 @@ struct KParams {
     long long n;          // cells
     long long pstride;    // elements between population planes
     int wall_y;
+    int wall_fixed;       // walls carry the constant psi_wall (ghost rows filled once), not a mirror
     // padded psi array: ghost layer of 1 in y (and z for 3-D), gx in x
     int px;               // row pitch in elements
     int py;               // rows per plane (ny + 2)
@@ -83,6 +85,8 @@ struct Launchers {
     const void *(*batch_kernel[2])();
     // balanced start: f^eq(rho, u0) -> f^eq(rho, u0 - F / (2 rho)) at even parity (psi of rho given)
     void (*rebalance)(const KParams &, void *A, const void *psi, cudaStream_t);
+    // wetting walls: psi_wall into the ghost rows y = -1 and y = ny of the padded psi field
+    void (*wall_fill)(const KParams &, void *psi, cudaStream_t);
     // single-pass step [BGK, MRT]: reads A (natural layout), pushes into B; NULL for FP64
     void (*fused[2])(const KParams &, const void *A, void *B, cudaStream_t);
 };

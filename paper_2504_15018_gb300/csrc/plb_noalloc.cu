@@ -56,6 +56,8 @@ extern "C" int plb_step_pairs_static(int lattice, const int dims[3], const plb_e
     int st = plb::check_create_args(lattice, dims, eos, tau, G, eps, opts, o, lay);
     if (st != PLB_OK) return st;
     if (o.streaming != PLB_STREAM_AA) return plb::set_error(PLB_EUNSUPPORTED, "this entry point steps in place (AA)");
+    if (o.wall_y && o.wall_rho > 0.0)
+        return plb::set_error(PLB_EUNSUPPORTED, "this entry point has neutral walls only (wall_rho <= 0)");
     if (!dev_pops) return plb::set_error(PLB_EINVAL, "dev_pops is NULL");
     if (reinterpret_cast<uintptr_t>(dev_pops) % 256 != 0)
         return plb::set_error(PLB_EINVAL, "dev_pops must be 256-byte aligned");

@@ -205,8 +205,9 @@ __device__ __forceinline__ void psi_ghosts(const KParams &p, float *psi, int x, 
     if (x == 0) xs[nxs++] = p.nx;
     ys[0] = y;
     if (p.wall_y) {
-        if (y == 0) ys[nys++] = -1;
-        if (y == p.ny - 1) ys[nys++] = p.ny;
+        // mirror rule; wetting walls keep the constant psi_wall written at creation
+        if (y == 0 && !p.wall_fixed) ys[nys++] = -1;
+        if (y == p.ny - 1 && !p.wall_fixed) ys[nys++] = p.ny;
     } else {
         if (y == p.ny - 1) ys[nys++] = -1;
         if (y == 0) ys[nys++] = p.ny;

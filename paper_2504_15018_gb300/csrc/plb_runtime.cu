@@ -205,6 +205,8 @@ int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos,
     if (o.collision != PLB_BGK && o.collision != PLB_MRT) return fail(PLB_EINVAL, "bad collision");
     if (o.tau_v > 0.0 && !(o.tau_v > 0.5)) return fail(PLB_EINVAL, "tau_v must be > 1/2");
     if (o.fp16_rounding != 0 && o.fp16_rounding != 1) return fail(PLB_EINVAL, "fp16_rounding must be 0 or 1");
+    if (o.wall_rho > 0.0 && !o.wall_y) return fail(PLB_EINVAL, "wall_rho needs walls (wall_y = 1)");
+    if (!std::isfinite(o.wall_rho)) return fail(PLB_EINVAL, "wall_rho must be finite");
     if (eos->kind == PLB_EOS_PR) {
         if (!(eos->a > 0 && eos->b > 0 && eos->R > 0 && eos->T_over_Tc > 0)) return fail(PLB_EINVAL, "bad PR constants");
     } else if (eos->kind == PLB_EOS_PAPER) {
@@ -226,6 +228,7 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
     k.n = lay.n;
     k.pstride = lay.pstride;
     k.wall_y = o.wall_y ? 1 : 0;
+    k.wall_fixed = (o.wall_y && o.wall_rho > 0.0) ? 1 : 0;
     k.px = lay.px;
     k.py = lay.py;
     k.psi_origin = lay.gx + (long long)lay.px * (1 + (long long)lay.py * (lay.D == 3 ? 1 : 0));
@@ -269,6 +272,12 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
         d.pe_sv = std::sqrt(eos.rho_v);
     }
     d.p_scale = eos.p_scale;
+    if (k.wall_fixed) {
+        // Eq. Interaction_Potential at the wall density
+        const double arg = 2.0 * (eos.p_scale * eos_pressure_host(eos, o.wall_rho) - o.wall_rho / 3.0) / G;
+        if (!(arg >= 0.0)) return fail(PLB_EINVAL, "psi is not defined at wall_rho for this EOS");
+        d.psi_wall = std::sqrt(arg);
+    }
     k.stochastic = o.precision == PLB_FP16S && o.fp16_rounding == 1;
     k.salt = 0;
     // FP32 copy (rounded once here, not per thread)
@@ -337,9 +346,13 @@ int plb_create(int lattice, const int dims[3], const plb_eos_params *eos, double
     k.flags = reinterpret_cast<unsigned *>(h->ws + lay.off_flags);
     cudaError_t e = cudaMemsetAsync(h->psi, 0, (size_t)lay.psi_elems * lay.s_psi, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(k.flags, 0, 64, h->stream);
+    if (e == cudaSuccess && k.wall_fixed) {
+        h->L->wall_fill(k, h->psi, h->stream);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         delete h;
-        return fail(PLB_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+        return fail(PLB_ECUDA, "workspace set-up: %s", cudaGetErrorString(e));
     }
     *out = h;
     return PLB_OK;

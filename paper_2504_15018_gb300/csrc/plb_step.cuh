@@ -385,8 +385,9 @@ __device__ __forceinline__ void psi_body(const KParams &p, const Planes<S> &A, t
         if (g.x == 0) xs[nxs++] = p.nx;
         ys[0] = g.y;
         if (p.wall_y) {
-            if (g.y == 0) ys[nys++] = -1;
-            if (g.y == p.ny - 1) ys[nys++] = p.ny;
+            // mirror rule; wetting walls keep the constant psi_wall written at creation
+            if (g.y == 0 && !p.wall_fixed) ys[nys++] = -1;
+            if (g.y == p.ny - 1 && !p.wall_fixed) ys[nys++] = p.ny;
         } else {
             if (g.y == p.ny - 1) ys[nys++] = -1;
             if (g.y == 0) ys[nys++] = p.ny;

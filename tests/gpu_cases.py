@@ -61,7 +61,7 @@ def oracle_params(case, rv, rl):
                               G=case.get("G", -1.0), eps=case.get("eps", 2.0), kappa=case.get("kappa", 1.0),
                               tau=case.get("tau", 1.0), tau_v=case.get("tau_v"), tau_rho=(rv, rl),
                               mrt=case.get("mrt", False), rates=case.get("rates"), fext=case.get("fext", (0, 0, 0)),
-                              p_scale=case.get("p_scale", 1.0))
+                              p_scale=case.get("p_scale", 1.0), wall_rho=case.get("wall_rho", 0.0))
 
 
 def make_lattice(case, rv, rl):
@@ -83,6 +83,8 @@ def make_lattice(case, rv, rl):
         kw.update(fp16_rounding=case["fp16_rounding"])
     if case.get("streaming"):
         kw.update(streaming=case["streaming"])
+    if case.get("wall_rho"):
+        kw.update(wall_rho=case["wall_rho"])
     return plb.Lattice(case["lattice"], case["dims"], eos, tau=case.get("tau", 1.0), G=case.get("G", -1.0),
                        eps=case.get("eps", 2.0), opts=plb.make_opts(**kw))
 

@@ -26,6 +26,8 @@ def _instances(lattice, specs, precision, mrt):
                   body_force=sp.get("fext", (0.0, 0.0, 0.0)), **RATES)
         if sp.get("tau_v"):
             kw.update(tau_v=sp["tau_v"], tau_rho_v=rv, tau_rho_l=rl)
+        if sp.get("wall_rho"):
+            kw.update(wall_rho=sp["wall_rho"])
         opts = plb.make_opts(**kw)
         dims = sp["dims"]
         out.append(plb.make_instance(dims, plb.pr_eos(t), tau=sp.get("tau", 1.0), opts=opts))
@@ -252,3 +254,22 @@ def test_batch96_workload_matches_lone_instances_and_translates_droplets():
         assert err < 0.02 * np.abs(want).max() + 0.25, (k, c1 - c0, want)
         checked += 1
     assert checked >= 3
+
+
+def test_batch_with_wetting_walls_matches_instances_stepped_alone():
+    """Instances with wetting walls (the wall rows of their psi fields filled at creation) next
+    to neutral-wall and periodic ones."""
+    import paper_2504_15018_gb300 as plb
+    specs = [dict(dims=(40, 24, 1), wall=True, shape="slab", wall_rho=1.2, fext=(1e-5, 0, 0)),
+             dict(dims=(37, 20, 1), wall=True, shape="slab", wall_rho=0.6, t_ratio=0.75),
+             dict(dims=(32, 32, 1), wall=True, shape="slab"),
+             dict(dims=(30, 26, 1), t_ratio=0.85)]
+    insts, fields = _instances(0, specs, 1, True)
+    b = plb.Batch(plb.PLB_D2Q9, insts)
+    for k, (rho, u0) in enumerate(fields):
+        b.init(k, rho, u0)
+    b.configure(tile_cells=256)
+    b.step(11)
+    b.status()
+    for k, (rho, u0) in enumerate(fields):
+        assert np.array_equal(b.populations(k), _alone(0, insts[k], rho, u0, 11)), k

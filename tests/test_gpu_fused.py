@@ -28,6 +28,10 @@ CASES = {
     "d3q19_fp16s_sr_mrt_walls": dict(lattice=1, dims=(34, 18, 12), wall=True, shape="slab", mrt=True, rates=RATES,
                                      precision=2, fp16_rounding=1),
     "d2q9_fp16s_bgk_droplet": dict(lattice=0, dims=(80, 70, 1), precision=2),
+    "d3q19_fp32_mrt_wetting_walls": dict(lattice=1, dims=(24, 20, 10), wall=True, shape="slab", mrt=True,
+                                         rates=RATES, wall_rho=0.9, precision=1),
+    "d2q9_fp16s_bgk_wetting_walls": dict(lattice=0, dims=(66, 34, 1), wall=True, shape="slab", wall_rho=1.2,
+                                         precision=2),
 }
 
 

@@ -25,6 +25,11 @@ FP64_CASES = {
                                  fext=(2e-6, 0, 1e-6)),
     "d3q19_mrt_periodic_droplet_u0": dict(lattice=1, dims=(12, 9, 11), mrt=True, rates=RATES, u0=(0.02, -0.01, 0.015),
                                           tau=0.9),
+    # wetting walls: psi on the wall nodes fixed at psi(wall_rho)
+    "d2q9_bgk_wetting_walls": dict(lattice=0, dims=(26, 22, 1), wall=True, shape="slab", wall_rho=1.2,
+                                   fext=(2e-6, 0, 0)),
+    "d3q19_mrt_wetting_walls": dict(lattice=1, dims=(11, 14, 8), wall=True, mrt=True, rates=RATES, shape="slab",
+                                    wall_rho=0.9),
 }
 
 # Even nx: FP32 / FP16S storage runs the two-cells-per-thread kernels on these.
@@ -234,3 +239,20 @@ def test_init_physical_matches_the_balanced_oracle_start(name):
     lat32.init(rho, u0, physical=True)
     _, u32, _ = lat32.moments()
     assert np.max(np.abs(u32[:d] - want)) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["d2q9_bgk_wetting_walls", "d3q19_mrt_wetting_walls"])
+def test_wetting_walls_fp32_pair_path_and_rejections(name):
+    """Wetting walls on the two-cell FP32 path (even nx) against the oracle after 200 steps
+    (linear FP32 accumulation bound), and the arguments the library refuses."""
+    import paper_2504_15018_gb300 as plb
+    case = dict(FP64_CASES[name], precision=1)
+    case["dims"] = (case["dims"][0] + case["dims"][0] % 2,) + tuple(case["dims"][1:])
+    ref, got, _, _ = run_both(case, 200)
+    assert max_rel_err(ref, got) <= 200 * 8 * 2.0 ** -24
+    with pytest.raises(plb.PlbError) as e:                       # wetting needs walls
+        plb.Lattice(0, (16, 16, 1), plb.pr_eos(0.8), opts=plb.make_opts(wall_rho=1.0))
+    assert e.value.code == plb.PLB_EINVAL
+    with pytest.raises(plb.PlbError) as e:                       # psi undefined at this density
+        plb.Lattice(0, (16, 16, 1), plb.pr_eos(0.8), opts=plb.make_opts(wall_y=1, wall_rho=10.4))
+    assert e.value.code == plb.PLB_EINVAL

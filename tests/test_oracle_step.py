@@ -407,3 +407,46 @@ def test_galilean_invariance_error_falls_at_second_order():
     orders = [math.log2(a / b) for a, b in zip(n1, n2)]
     assert min(orders) > 1.8, (n1, n2, orders)
     assert n1[1] < 0.06
+
+
+def _pr08():
+    a, b, om = 2 / 49, 2 / 21, 0.327
+    T = 0.8 * pp.pr_Tc(a, b)
+    eos = dict(kind="pr", a=a, b=b, R=1.0, omega=om, T=T)
+    mv, ml, _ = pp.mechanical_stability(lambda r: pp.pr_pressure(r, a, b, 1.0, om, T), -1.0, 2.0, rho_max=0.999 / b)
+    return eos, mv, ml
+
+
+def test_wetting_wall_at_the_fluid_density_exerts_no_force():
+    """Wetting walls (psi on the wall nodes = psi(wall_rho)): a uniform fluid at rest between
+    walls whose density equals the fluid's sees the same psi everywhere, so every force
+    vanishes and it stays exactly at rest; any other wall density attracts or repels the
+    first rows and the fluid layers."""
+    eos, _, _ = _pr08()
+    P = oracle.make_params(0, (6, 10, 1), wall_y=True, eos=eos, wall_rho=7.0)
+    r, u, _ = oracle.moments(P, oracle.run(P, oracle.init(P, np.full(60, 7.0)), 200))
+    assert np.abs(r - 7.0).max() == 0.0 and np.abs(u).max() == 0.0
+    P = oracle.make_params(0, (6, 10, 1), wall_y=True, eos=eos, wall_rho=3.5)
+    r, u, _ = oracle.moments(P, oracle.run(P, oracle.init(P, np.full(60, 7.0)), 200))
+    assert np.abs(r - 7.0).max() > 0.1
+    # the layering is symmetric between the two walls
+    rr = r.reshape(10, 6)[:, 0]
+    assert np.allclose(rr, rr[::-1], rtol=1e-12)
+
+
+def test_wetting_wall_contact_width_grows_with_wall_density():
+    """A droplet on the lower wall (48 x 24, PR T/Tc = 0.8): the higher the wall density,
+    the wider the liquid's contact with the wall and the flatter the droplet; a wall at a
+    vapour-like density lifts the droplet off the wall (no liquid in the rows next to it)."""
+    eos, mv, ml = _pr08()
+    nx, ny = 48, 24
+    mid = 0.5 * (mv + ml)
+    widths, heights = [], []
+    for wr in (1.5, 1.0, 0.5):
+        rho = inputs.droplet((nx, ny, 1), (nx / 2, 0.5), 8, mv, ml, 3.0, periodic=False)
+        P = oracle.make_params(0, (nx, ny, 1), wall_y=True, eos=eos, wall_rho=wr)
+        r = oracle.moments(P, oracle.run(P, oracle.init(P, rho), 5000))[0].reshape(ny, nx)
+        widths.append(int((r[1] > mid).sum()))
+        heights.append(int((r[:, nx // 2] > mid).sum()))
+    assert widths[0] > widths[1] > widths[2] == 0, widths
+    assert heights[0] < heights[1] < heights[2], heights
