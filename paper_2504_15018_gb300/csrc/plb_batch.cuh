@@ -1,6 +1,7 @@
 // Persistent kernel of a batch of independent lattices: every step runs the psi pass over
 // all tiles of all instances, a grid barrier, the fused force/collide/stream pass, and a
-// second barrier, for nsteps steps in one launch.  Loads go through L2 only (LdCoherent):
+// second barrier, for nsteps steps in one launch.  Loads follow LdBatch (populations through
+// L2 only, the psi stencil through L1 after the barrier's acquire):
 // blocks read, across barriers, what other SMs wrote in the same launch.
 #pragma once
 #include "plb_pair.cuh"
@@ -61,13 +62,13 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
                 geo_pair_at(p, 2 * xu, y, tl.z, g);
                 float *psi = static_cast<float *>(in.psi);
                 if (PSI) {
-                    if (!odd) psi_pair_body<L, S, false, false, LdCoherent>(p, A, psi, g);
-                    else if (wall) psi_pair_body<L, S, true, true, LdCoherent>(p, A, psi, g);
-                    else psi_pair_body<L, S, true, false, LdCoherent>(p, A, psi, g);
+                    if (!odd) psi_pair_body<L, S, false, false, LdBatch>(p, A, psi, g);
+                    else if (wall) psi_pair_body<L, S, true, true, LdBatch>(p, A, psi, g);
+                    else psi_pair_body<L, S, true, false, LdBatch>(p, A, psi, g);
                 } else {
-                    if (!odd) collide_pair_body<L, S, MRT, false, false, LdCoherent, SR>(p, A, psi, g, salt);
-                    else if (wall) collide_pair_body<L, S, MRT, true, true, LdCoherent, SR>(p, A, psi, g, salt);
-                    else collide_pair_body<L, S, MRT, true, false, LdCoherent, SR>(p, A, psi, g, salt);
+                    if (!odd) collide_pair_body<L, S, MRT, false, false, LdBatch, SR>(p, A, psi, g, salt);
+                    else if (wall) collide_pair_body<L, S, MRT, true, true, LdBatch, SR>(p, A, psi, g, salt);
+                    else collide_pair_body<L, S, MRT, true, false, LdBatch, SR>(p, A, psi, g, salt);
                 }
                 done = true;
             }
@@ -77,13 +78,13 @@ __device__ __forceinline__ void batch_tile(const BatchInst &in, const BatchTile 
             geo_at<int>(p, xu, y, tl.z, g);
             PsiT *psi = static_cast<PsiT *>(in.psi);
             if (PSI) {
-                if (!odd) psi_body<L, S, false, false, LdCoherent>(p, A, psi, g);
-                else if (wall) psi_body<L, S, true, true, LdCoherent>(p, A, psi, g);
-                else psi_body<L, S, true, false, LdCoherent>(p, A, psi, g);
+                if (!odd) psi_body<L, S, false, false, LdBatch>(p, A, psi, g);
+                else if (wall) psi_body<L, S, true, true, LdBatch>(p, A, psi, g);
+                else psi_body<L, S, true, false, LdBatch>(p, A, psi, g);
             } else {
-                if (!odd) collide_body<L, S, MRT, false, false, LdCoherent, SR>(p, A, psi, g, salt);
-                else if (wall) collide_body<L, S, MRT, true, true, LdCoherent, SR>(p, A, psi, g, salt);
-                else collide_body<L, S, MRT, true, false, LdCoherent, SR>(p, A, psi, g, salt);
+                if (!odd) collide_body<L, S, MRT, false, false, LdBatch, SR>(p, A, psi, g, salt);
+                else if (wall) collide_body<L, S, MRT, true, true, LdBatch, SR>(p, A, psi, g, salt);
+                else collide_body<L, S, MRT, true, false, LdBatch, SR>(p, A, psi, g, salt);
             }
         }
     }

@@ -140,6 +140,14 @@ struct LdCoherent {
     template <class U> __device__ __forceinline__ static U ld(const U *a) { return __ldcg(a); }
     template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldcg(a); }
 };
+// LdBatch: the persistent batch kernel after a grid barrier.  The barrier is a release /
+// acquire pattern at GPU scope (atomic arrival and __threadfence on both sides, then a block
+// barrier), so ordinary L1-cached loads issued after it observe the other blocks' writes.
+// Populations are read once and bypass L1; the psi stencil, read by several threads, is cached.
+struct LdBatch {
+    template <class U> __device__ __forceinline__ static U ld(const U *a) { return __ldcg(a); }
+    template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldca(a); }
+};
 
 template <class S> struct Store;
 template <> struct Store<double> {
