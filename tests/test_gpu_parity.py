@@ -101,7 +101,7 @@ def test_fp16s_population_parity(name):
     over n steps add like a random walk: bound sqrt(n) * 2^-11 relative to w_i rho_l.  The
     horizon is 50 steps: later, the relaxing interfaces of the walled slab amplify any
     perturbation (FP32 and the one-cell-per-thread FP16 kernel grow the same way), and FP16 is
-    judged on the macroscopic results instead (tests/test_gpu_precision.py)."""
+    assessed on the macroscopic results instead (tests/test_gpu_precision.py)."""
     case = dict({**FP64_CASES, **PAIR_CASES}[name], precision=2)
     steps = 50
     ref, got, _, _ = run_both(case, steps)

@@ -279,7 +279,7 @@ def test_plates_velocity_profile_all_precisions():
     """Plate velocity profile per storage precision against FP64, and FP64 against the steady
     channel flow of its own density profile (mu(y) = rho(y) / 6 at tau = 1, interpolated
     linearly between cell centres).  F = 1e-7 changes a liquid population by ~1.6e-8 per step,
-    about one FP32 ulp and 1e-4 of an FP16 ulp, so the storage precisions are judged by how
+    about one FP32 ulp and 1e-4 of an FP16 ulp, so the storage precisions are assessed by how
     much of the profile they keep (relative L2 against FP64, reported; FP32 asserted within
     2 %, FP16S with stochastic rounding within 25 %)."""
     from oracle import params as pp
