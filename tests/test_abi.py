@@ -125,3 +125,31 @@ def test_create_rejects_bad_arguments_without_touching_the_device(L):
     with pytest.raises(plb.PlbError) as e:
         plb.plb_create(plb.PLB_D2Q9, dims, eos, 1.0, -1.0, 2.0, o, fake, nbytes - 1, 0)
     assert e.value.code == plb.PLB_ENOMEM
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of plb_eos_params, plb_opts and plb_instance have the size and the
+    field offsets the C compiler gives the header's structs (a C program built with gcc
+    against include/plb.h prints them)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"plb_eos_params": plb.plb_eos_params, "plb_opts": plb.plb_opts, "plb_instance": plb.plb_instance}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "plb.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
