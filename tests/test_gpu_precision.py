@@ -334,3 +334,29 @@ def test_contact_angle_follows_the_wall_density():
     assert angles[0] < angles[1] < angles[2], angles
     # the mirror rule makes the wall a symmetry plane of the psi field: about 90 degrees
     assert 75.0 < angles[3] < 105.0
+
+
+def test_plates_full_size_equals_the_cross_section():
+    """The D3Q19 plates workload at full size (512 x 256 x 256, FP32, MRT, 50,000 steps).  Its
+    initial state is invariant in x and z and every cell runs the same arithmetic, so it must
+    equal the 4 x 256 x 4 cross-section (whose profile the test above compares with FP64 and the
+    channel flow) bit for bit in every column."""
+    import paper_2504_15018_gb300 as plb
+    rv, rl, _ = maxwell(0.8)
+    out = []
+    for dims in ((4, 256, 4), (512, 256, 256)):
+        d, rho = inputs.plates_d3q19(dims, rv, rl)
+        opts = plb.make_opts(precision=plb.PLB_FP32, collision=plb.PLB_MRT, wall_y=1, body_force=(1e-7, 0.0, 0.0),
+                             **MRT_RATES)
+        lat = plb.Lattice(plb.PLB_D3Q19, d, plb.pr_eos(0.8), 1.0, -1.0, 2.0, opts=opts)
+        lat.init(rho)
+        lat.step(50000)
+        lat.status()
+        r, u, _ = lat.moments()
+        shape = (dims[2], dims[1], dims[0])
+        out.append((r.reshape(shape), u[0].reshape(shape)))
+        del lat
+    (r4, u4), (rf, uf) = out
+    assert np.array_equal(rf, np.broadcast_to(r4[:1, :, :1], rf.shape))
+    assert np.array_equal(uf, np.broadcast_to(u4[:1, :, :1], uf.shape))
+    print(f"full size after 50000 steps: umax {uf.max():.4e}, equal to the cross-section in every column")
