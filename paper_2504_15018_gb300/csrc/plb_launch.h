@@ -36,6 +36,8 @@ struct KParams {
     int var_tau;
     int eos_kind;         // 0 PR, 1 paper
     int stochastic;       // FP16 stores with stochastic rounding
+    int prefetch_ahead;   // k_collide_pair: prefetch into L2 for the block this many launch slots later (0: off)
+    int pf_step[3];       // that offset split along the grid axes (x, y, z), for carry propagation
     unsigned salt;        // step counter mixed into the rounding noise
     Phys<double> d;
     Phys<float> f;

@@ -298,9 +298,29 @@ __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes
     store_pair<L, S, ODD, WALL, SR>(p, A, g, f, salt);
 }
 
+// L2 prefetch of the populations of the cell pair that the same thread of the block
+// `ahead` launch slots later will update (blocks start roughly in linear order), so that one
+// wave of blocks has the next wave's loads in flight without holding them in registers.
+template <class L, class S>
+__device__ __forceinline__ void prefetch_ahead_pair(const KParams &p, const Planes<S> &A) {
+    // block index + prefetch_ahead in linear launch order, from its per-axis parts with carries
+    int bx = blockIdx.x + p.pf_step[0], by = blockIdx.y + p.pf_step[1], bz = blockIdx.z + p.pf_step[2];
+    if (bx >= (int)gridDim.x) { bx -= gridDim.x; ++by; }
+    if (by >= (int)gridDim.y) { by -= gridDim.y; ++bz; }
+    if (bz >= (int)gridDim.z) return;
+    const int x0 = 2 * (bx * blockDim.x + threadIdx.x), y = by * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    const int s0 = x0 + p.nx * (y + p.ny * bz);
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(A.p[i] + s0));
+    });
+}
+
 template <class L, class S, int MRT, bool ODD>
 __global__ void __launch_bounds__(256, PLB_PAIR_MINB) k_collide_pair(KParams p, Planes<S> A,
                                                                     const float *__restrict__ psi) {
+    if (p.prefetch_ahead > 0) prefetch_ahead_pair<L, S>(p, A);
     GeoPair g;
     if (!make_geo_pair(p, g)) return;
     const bool wall = ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1);
