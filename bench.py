@@ -160,7 +160,7 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_pair.cuh", "plb_step.cuh")
+KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_kernels.cuh", "plb_pair.cuh", "plb_step.cuh")
 
 
 def kernel_source_sha():

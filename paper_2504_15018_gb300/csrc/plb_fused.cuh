@@ -12,7 +12,7 @@
 // Populations live in two copies: the kernel reads A (natural layout, f_i(x) at A[i][x]) and
 // pushes the post-collision populations into B (B[i][x + c_i], halfway bounce-back at the y
 // walls), so no block can read a population another block has already overwritten.  The
-// per-cell arithmetic (psi_pair_of, force_pair_from, collide_fast) is the same code as the
+// per-cell arithmetic (psi_pair_of, force_pair_from, collide_store_pair) is the same code as the
 // two-pass kernels, so both give the same populations bit for bit.
 #pragma once
 #include "plb_pair.cuh"
@@ -93,18 +93,17 @@ __device__ __forceinline__ void fused_collide_plane(const KParams &p, const Plan
         };
         f2 F[3];
         force_pair_from<L>(p, at, F);
-        collide_fast<L, MRT, Store<S>::SHIFT, f2>(p, f, F);
         // push streaming into B: the odd-parity store of the two-pass kernels
         if (p.wall_y && (y == 0 || y == p.ny - 1))
-            store_pair<L, S, true, true, SR>(p, B, g, f, salt);
+            collide_store_pair<L, S, MRT, true, true, SR>(p, B, g, f, F, salt);
         else
-            store_pair<L, S, true, false, SR>(p, B, g, f, salt);
+            collide_store_pair<L, S, MRT, true, false, SR>(p, B, g, f, F, salt);
     }
 }
 
 // Grid: (ceil(nx / TX), ceil(ny / TY), ceil(nz / zc)); block: THREADS threads.
 template <class L, class S, int MRT, bool SR>
-__global__ void __launch_bounds__(256, PLB_PAIR_MINB) k_fused_pair(KParams p, Planes<S> A, Planes<S> B, int zc) {
+__global__ void __launch_bounds__(256, 2) k_fused_pair(KParams p, Planes<S> A, Planes<S> B, int zc) {
     using Tl = FusedTile<L>;
     constexpr int PLANE = Tl::RY * 2 * Tl::HP;
     __shared__ __align__(16) float ring[Tl::NPL * PLANE];

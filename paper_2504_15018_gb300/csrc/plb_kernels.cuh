@@ -15,6 +15,10 @@
 #ifndef PLB_L2_PREFETCH
 #define PLB_L2_PREFETCH 1
 #endif
+// L2 prefetch distance of the FP32 fused pass in waves of resident blocks.
+#ifndef PLB_PF_WAVES
+#define PLB_PF_WAVES 1
+#endif
 // Two cells per thread for FP16 storage (1) or one (0).
 #ifndef PLB_HALF_PAIR
 #define PLB_HALF_PAIR 1
@@ -279,10 +283,11 @@ template <class L, class S> struct Launch {
         if (std::is_same<S, __half>::value && !PLB_HALF_PAIR) return false;
         return !std::is_same<S, double>::value && (p.nx % 2 == 0) && p.n < (1LL << 31);
     }
-    static void dims_pair(const KParams &p, dim3 &grid, dim3 &block) {
+    static void dims_pair(const KParams &p, dim3 &grid, dim3 &block, int threads = 256) {
         const int npx = p.nx / 2;
-        int bx = npx >= 256 ? 256 : (npx + 31) / 32 * 32;
-        int by = 256 / bx;
+        int bx = npx >= threads ? threads : (npx + 31) / 32 * 32;
+        if (threads & (threads - 1)) bx = npx >= 64 ? 64 : (npx + 31) / 32 * 32;   // 64 wide
+        int by = threads / bx;
         if (by > p.ny) by = p.ny;
         block = dim3(bx, by, 1);
         grid = dim3((npx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
@@ -306,23 +311,42 @@ template <class L, class S> struct Launch {
         if (odd) psi_t<true>(p, A, psi, st);
         else psi_t<false>(p, A, psi, st);
     }
+    // resident blocks per SM of the pair collide kernel (one wave = this x SM count)
+    template <int MRT, bool ODD> static int pair_blocks_per_sm() {
+        static int nb = 0;
+        if (nb == 0) {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_collide_pair<L, S, MRT, ODD, false>,
+                                                              PLB_PAIR_THREADS, 0) != cudaSuccess || v < 1)
+                v = 1;
+            nb = v;
+        }
+        return nb;
+    }
     template <int MRT, bool ODD> static void collide_t(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         dim3 grid, block;
         if constexpr (!std::is_same<S, double>::value) {
             if (use_pair(p)) {
-                dims_pair(p, grid, block);
-                // FP32 storage: prefetch into L2 for the block one wave (two resident blocks on
-                // every SM) later, +3 % on the fused pass; FP16S is bound by arithmetic and
-                // loses more to the extra instructions than it gains
+                dims_pair(p, grid, block, PLB_PAIR_THREADS);
+                // FP32 storage: prefetch into L2 for the block one wave (the resident blocks of
+                // every SM) later; FP16S is bound by arithmetic and loses more to the extra
+                // instructions than it gains
                 KParams q = p;
                 if (std::is_same<S, float>::value && PLB_L2_PREFETCH) {
-                    const int ahead = 2 * sm_count();
+                    const int ahead = PLB_PF_WAVES * pair_blocks_per_sm<MRT, ODD>() * sm_count();
                     q.prefetch_ahead = ahead;
                     q.pf_step[0] = ahead % (int)grid.x;
                     q.pf_step[1] = (ahead / (int)grid.x) % (int)grid.y;
                     q.pf_step[2] = ahead / ((int)grid.x * (int)grid.y);
                 }
-                k_collide_pair<L, S, MRT, ODD><<<grid, block, 0, st>>>(q, planes(p, A), (const float *)psi);
+                if constexpr (Store<S>::SHIFT) {
+                    if (p.stochastic) {
+                        k_collide_pair<L, S, MRT, ODD, true><<<grid, block, 0, st>>>(q, planes(p, A),
+                                                                                    (const float *)psi);
+                        return;
+                    }
+                }
+                k_collide_pair<L, S, MRT, ODD, false><<<grid, block, 0, st>>>(q, planes(p, A), (const float *)psi);
                 return;
             }
         }

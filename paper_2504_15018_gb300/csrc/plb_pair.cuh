@@ -110,32 +110,39 @@ __device__ __forceinline__ void load_pair(const KParams &p, const Planes<S> &A, 
     });
 }
 
-template <class L, class S, bool ODD, bool WALL, bool SR = false>
-__device__ __forceinline__ void store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, const f2 *f,
-                                           unsigned salt = 0) {
-    unsigned hsh = 0;
-    if constexpr (SR) hsh = cell_hash((unsigned)g.s0, salt);
-    Unroll<0, L::Q>::run([&](auto ic) {
-        constexpr int i = decltype(ic)::value;
-        constexpr int o = opp(i);
-        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        f2 v = f[i];
-        if constexpr (SR) v = PairIO<S>::dither(v, dir_bits(hsh, i));
-        if (!ODD) {
+// Population I of the pair to its place: the aligned slot of the opposite direction on even
+// steps; on odd steps the neighbour in direction c_I, or, across a wall, the opposite slot of
+// the cell itself (halfway bounce-back).  hsh: the pair's random bits (SR).
+template <class L, class S, bool ODD, bool WALL, bool SR, int I>
+__device__ __forceinline__ void store_dir(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 v,
+                                          unsigned hsh) {
+    constexpr int o = opp(I);
+    constexpr int cx = L::cx(I), cy = L::cy(I), cz = L::cz(I);
+    if constexpr (SR) v = PairIO<S>::dither(v, dir_bits(hsh, I));
+    if (!ODD) {
+        PairIO<S>::st2(A.p[o] + g.s0, v);
+    } else {
+        bool to_wall = false;
+        if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
+        if (to_wall) {
             PairIO<S>::st2(A.p[o] + g.s0, v);
         } else {
-            bool to_wall = false;
-            if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
-            if (to_wall) {
-                PairIO<S>::st2(A.p[o] + g.s0, v);
-            } else {
-                const int r = g.s0 + g.oy[1 + cy] + g.oz[1 + cz];
-                if (cx == 0)
-                    PairIO<S>::st2(A.p[i] + r, v);
-                else
-                    PairIO<S>::st11(A.p[i] + (r + g.ox0[1 + cx]), A.p[i] + (r + 1 + g.ox1[1 + cx]), v);
-            }
+            const int r = g.s0 + g.oy[1 + cy] + g.oz[1 + cz];
+            if (cx == 0)
+                PairIO<S>::st2(A.p[I] + r, v);
+            else
+                PairIO<S>::st11(A.p[I] + (r + g.ox0[1 + cx]), A.p[I] + (r + 1 + g.ox1[1 + cx]), v);
         }
+    }
+}
+
+// Collision of the pair with each population stored as soon as it is final (collide_emit).
+template <class L, class S, int MRT, bool ODD, bool WALL, bool SR>
+__device__ __forceinline__ void collide_store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 *f,
+                                                   const f2 F[3], unsigned salt) {
+    const unsigned hsh = SR ? cell_hash((unsigned)g.s0, salt) : 0u;
+    collide_emit<L, MRT, Store<S>::SHIFT, f2>(p, f, F, [&](auto ic, const f2 &v) {
+        store_dir<L, S, ODD, WALL, SR, decltype(ic)::value>(p, A, g, v, hsh);
     });
 }
 
@@ -283,9 +290,16 @@ __global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float 
         psi_pair_body<L, S, ODD, false>(p, A, psi, g);
 }
 
-#ifndef PLB_PAIR_MINB
-#define PLB_PAIR_MINB 2
+// Threads per block and register cap of the pair collide kernel: 64 threads and 112
+// registers leave 18 warps resident per SM (measured best for FP32 and FP16 storage against
+// 256 x 128, 128 x 96, 128 x 80 and 64 x 88).
+#ifndef PLB_PAIR_THREADS
+#define PLB_PAIR_THREADS 64
 #endif
+#ifndef PLB_PAIR_MAXREG
+#define PLB_PAIR_MAXREG 112
+#endif
+
 
 template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, bool SR = false>
 __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes<S> &A, const float *__restrict__ psi,
@@ -294,8 +308,7 @@ __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes
     load_pair<L, S, ODD, WALL, Pol>(p, A, g, f);
     f2 F[3];
     force_pair<L, Pol>(p, psi + psi_index(p, g.x0, g.y, g.z), F);
-    collide_fast<L, MRT, Store<S>::SHIFT, f2>(p, f, F);
-    store_pair<L, S, ODD, WALL, SR>(p, A, g, f, salt);
+    collide_store_pair<L, S, MRT, ODD, WALL, SR>(p, A, g, f, F, salt);
 }
 
 // L2 prefetch of the populations of the cell pair that the same thread of the block
@@ -317,24 +330,18 @@ __device__ __forceinline__ void prefetch_ahead_pair(const KParams &p, const Plan
     });
 }
 
-template <class L, class S, int MRT, bool ODD>
-__global__ void __launch_bounds__(256, PLB_PAIR_MINB) k_collide_pair(KParams p, Planes<S> A,
-                                                                    const float *__restrict__ psi) {
+// SR: stochastic rounding of the FP16 stores, a compile-time choice so that the
+// round-to-nearest kernel is register-allocated for its own path.
+template <class L, class S, int MRT, bool ODD, bool SR>
+__global__ void __maxnreg__(PLB_PAIR_MAXREG) k_collide_pair(KParams p, Planes<S> A, const float *__restrict__ psi) {
     if (p.prefetch_ahead > 0) prefetch_ahead_pair<L, S>(p, A);
     GeoPair g;
     if (!make_geo_pair(p, g)) return;
     const bool wall = ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1);
-    if constexpr (Store<S>::SHIFT) {
-        if (p.stochastic) {
-            if (wall) collide_pair_body<L, S, MRT, ODD, true, LdStream, true>(p, A, psi, g, p.salt);
-            else collide_pair_body<L, S, MRT, ODD, false, LdStream, true>(p, A, psi, g, p.salt);
-            return;
-        }
-    }
     if (wall)
-        collide_pair_body<L, S, MRT, ODD, true>(p, A, psi, g);
+        collide_pair_body<L, S, MRT, ODD, true, LdStream, SR>(p, A, psi, g, p.salt);
     else
-        collide_pair_body<L, S, MRT, ODD, false>(p, A, psi, g);
+        collide_pair_body<L, S, MRT, ODD, false, LdStream, SR>(p, A, psi, g, p.salt);
 }
 
 }  // namespace plb

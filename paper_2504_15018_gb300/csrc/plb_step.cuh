@@ -355,6 +355,132 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
     });
 }
 
+// The collision of collide_fast with its output streamed: emit(ic, v) receives the new stored
+// value of population decltype(ic)::value as soon as it is final, so that a pair's registers
+// are free once it is stored.  Equal to collide_fast in exact arithmetic (rounding differs).
+// BGK (any lattice) and D3Q19 MRT take the streamed form; D2Q9 MRT runs collide_fast and then
+// emits.  For D3Q19 MRT the ghost moments of g = f - feq + Ft/2 come first, from the pair sums
+// of the stored values and closed forms for the moments of feq and Ft, so no per-population g
+// is kept.  With v = j - F/2 (= rho u - F) and P_a = u_a v_a, the rows of the
+// d'Humieres et al. (2002) basis applied to the equilibrium and the Guo term of Sec. II give
+// (sums over the D3Q19 velocities):
+//   m_e(g)   = m_e(h)   + 11 drho - 19 u.v        m_eps(g) = m_eps(h) - 3 drho + 5.5 u.v
+//   m_pxx(g) = m_pxx(h) + P_x - (P_y + P_z) / 2   m_pww(g) = m_pww(h) + (P_y - P_z) / 2
+//   m_q(g)   = m_q(h)   + (2/3) j                 m_m(g)   = m_m(h)
+// where h is the stored value (f, or f - w rho_ref with the shift) and drho = sum_i h_i.
+template <class L, int MRT, bool SHIFT, class T, class Emit>
+__device__ __forceinline__ void collide_emit(const KParams &p, T *f, const T F[3], Emit &&emit) {
+    if constexpr (MRT && !std::is_same<L, D3Q19>::value) {
+        collide_fast<L, MRT, SHIFT, T>(p, f, F);
+        Unroll<0, L::Q>::run([&](auto ic) { emit(ic, f[decltype(ic)::value]); });
+    } else {
+        using R = typename ScalarOf<T>::type;
+        const Phys<R> &q = phys<R>(p);
+        constexpr int NP = (L::Q - 1) / 2;
+        T fs[NP], fa[NP];
+        T rho = f[0], j[3] = {T(0), T(0), T(0)};
+        Unroll<0, NP>::run([&](auto kc) {
+            constexpr int r = decltype(kc)::value;
+            constexpr int i = 2 * r + 1;
+            fs[r] = f[i] + f[i + 1];
+            fa[r] = f[i] - f[i + 1];
+            rho += fs[r];
+            add_c<L::cx(i)>(j[0], fa[r]);
+            add_c<L::cy(i)>(j[1], fa[r]);
+            add_c<L::cz(i)>(j[2], fa[r]);
+        });
+        const T drho = rho;                                // sum of the stored values
+        if (SHIFT) rho += T(q.rho_ref);
+        const T irho = fdiv(T(1), rho);
+        const T u[3] = {mad(T(0.5), F[0], j[0]) * irho, mad(T(0.5), F[1], j[1]) * irho,
+                        mad(T(0.5), F[2], j[2]) * irho};
+        const T om = omega_of<T>(p, rho);
+        const T nom = -om;
+        const T Bq = T(-1.5) * mad(u[0], u[0], mad(u[1], u[1], u[2] * u[2]));
+        const T nuF3 = T(-3) * mad(u[0], F[0], mad(u[1], F[1], u[2] * F[2]));
+        const T kguo = mad(T(-0.5), om, T(1));
+        // relaxation amplitudes A_k = (s_k - omega) m_k(g) / |M_k|^2 of the ghost rows (MRT)
+        T Ae, Aeps, Aqx, Aqy, Aqz, Apxx, Apww, Amx, Amy, Amz;
+        if constexpr (MRT) {
+            using G = Ghosts<D3Q19>;
+            const T sx = fs[0], sy = fs[1], sz = fs[2];
+            const T Dxy = fs[3] + fs[4], Dxz = fs[5] + fs[6], Dyz = fs[7] + fs[8];
+            const T syz = sy + sz;
+            const T S1 = sx + syz, S2 = Dxy + Dxz + Dyz;
+            const T Px = u[0] * mad(T(-0.5), F[0], j[0]), Py = u[1] * mad(T(-0.5), F[1], j[1]),
+                    Pz = u[2] * mad(T(-0.5), F[2], j[2]);
+            const T uv = Px + Py + Pz;
+            const T m_e = mad(T(-30), f[0], mad(T(-11), S1, mad(T(8), S2, mad(T(11), drho, T(-19) * uv))));
+            const T m_eps = mad(T(12), f[0], mad(T(-4), S1, S2 + mad(T(-3), drho, T(5.5) * uv)));
+            const T m_pxx = mad(T(-4), sx, mad(T(2), syz, mad(T(-2), Dyz, (Dxy + Dxz) + mad(T(-0.5), Py + Pz, Px))));
+            const T m_pww = mad(T(2), sz - sy, (Dxy - Dxz) + T(0.5) * (Py - Pz));
+            const T Pxy = fa[3] + fa[4], Qxy = fa[3] - fa[4];
+            const T Pxz = fa[5] + fa[6], Qxz = fa[5] - fa[6];
+            const T Pyz = fa[7] + fa[8], Qyz = fa[7] - fa[8];
+            const T m_qx = mad(T(-4), fa[0], mad(T(2.0 / 3.0), j[0], Pxy + Pxz)), m_mx = Pxy - Pxz;
+            const T m_qy = mad(T(-4), fa[1], mad(T(2.0 / 3.0), j[1], Qxy + Pyz)), m_my = Pyz - Qxy;
+            const T m_qz = mad(T(-4), fa[2], mad(T(2.0 / 3.0), j[2], Qxz + Qyz)), m_mz = Qxz - Qyz;
+            auto A = [&](int k, const T &m) {
+                return (T(q.s_rate[G::kind(k)]) - om) * (T(1.0 / row_norm2<D3Q19>(k)) * m);
+            };
+            Ae = A(0, m_e), Aeps = A(1, m_eps), Aqx = A(2, m_qx), Aqy = A(3, m_qy), Aqz = A(4, m_qz);
+            Apxx = A(5, m_pxx), Apww = A(6, m_pww), Amx = A(7, m_mx), Amy = A(8, m_my), Amz = A(9, m_mz);
+        }
+        // rest population
+        {
+            constexpr double w = wcol<L, R>(0);
+            const T dn = mad(T(-w) * rho, Bq, mad(T(-w), drho, f[0]));       // f - feq
+            T v = mad(kguo * T(w), nuF3, mad(nom, dn, f[0]));
+            if constexpr (MRT) v -= mad(T(-30), Ae, T(12) * Aeps);
+            emit(std::integral_constant<int, 0>{}, v);
+        }
+        // opposite pair r = (i, i + 1): c_{i+1} = -c_i, the first non-zero component of c_i is +1
+        Unroll<0, NP>::run([&](auto kc) {
+            constexpr int r = decltype(kc)::value;
+            constexpr int i = 2 * r + 1;
+            constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            constexpr double w = wcol<L, R>(i);
+            const T cu = dot_c<cx, cy, cz>(u);
+            const T cF = dot_c<cx, cy, cz>(F);
+            const T S = mad(T(4.5) * cu, cu, Bq);
+            const T Gs = mad(T(9) * cu, cF, nuF3);
+            const T dns = mad(T(-2 * w) * rho, S, mad(T(-2 * w), drho, fs[r]));   // sum of f - feq
+            const T dna = mad(T(-6 * w) * rho, cu, fa[r]);                        // difference
+            T vs = mad(kguo * T(2 * w), Gs, mad(nom, dns, fs[r]));
+            T va = mad(kguo * T(6 * w), cF, mad(nom, dna, fa[r]));
+            if constexpr (MRT) {
+                // back-projection f_i -= sum_k M_ki A_k by velocity class (pairs: 0-2 axes x, y,
+                // z; 3, 4: (1, +-1, 0); 5, 6: (1, 0, +-1); 7, 8: (0, 1, +-1))
+                const T C1 = mad(T(-11), Ae, T(-4) * Aeps), C2 = mad(T(8), Ae, Aeps);
+                T E, O;
+                if constexpr (r == 0) { E = mad(T(-4), Apxx, C1); O = T(-4) * Aqx; }
+                if constexpr (r == 1) { E = mad(T(-2), Apww, mad(T(2), Apxx, C1)); O = T(-4) * Aqy; }
+                if constexpr (r == 2) { E = mad(T(2), Apww, mad(T(2), Apxx, C1)); O = T(-4) * Aqz; }
+                if constexpr (r == 3 || r == 4) {
+                    E = (C2 + Apxx) + Apww;
+                    const T a = Aqx + Amx, b = Aqy - Amy;
+                    O = r == 3 ? a + b : a - b;
+                }
+                if constexpr (r == 5 || r == 6) {
+                    E = (C2 + Apxx) - Apww;
+                    const T a = Aqx - Amx, b = Aqz + Amz;
+                    O = r == 5 ? a + b : a - b;
+                }
+                if constexpr (r == 7 || r == 8) {
+                    E = mad(T(-2), Apxx, C2);
+                    const T a = Aqy + Amy, b = Aqz - Amz;
+                    O = r == 7 ? a + b : a - b;
+                }
+                vs = mad(T(-2), E, vs);
+                va = mad(T(-2), O, va);
+            }
+            const T hs = T(0.5) * vs;
+            emit(std::integral_constant<int, i>{}, mad(T(0.5), va, hs));
+            emit(std::integral_constant<int, i + 1>{}, mad(T(-0.5), va, hs));
+        });
+    }
+}
+
 // ------------------------------------------------------------------ kernels
 // Minimum resident 256-thread blocks per SM requested from the register allocator.
 #ifndef PLB_COLLIDE_MINB
