@@ -294,7 +294,7 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants:
         combos = [("fp16s", "fused"), ("fp16s_sr", "fused"), ("fp32", "fused"), ("fp32", "aa"), ("fp16s", "aa"),
-                  ("fp64", "aa")]
+                  ("fp16s_sr", "aa"), ("fp64", "aa")]
         for prec, strm in combos:
             if (prec, strm) == (args.precision, args.streaming):
                 continue

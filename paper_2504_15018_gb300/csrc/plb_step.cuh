@@ -358,8 +358,8 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
 // The collision of collide_fast with its output streamed: emit(ic, v) receives the new stored
 // value of population decltype(ic)::value as soon as it is final, so that a pair's registers
 // are free once it is stored.  Equal to collide_fast in exact arithmetic (rounding differs).
-// BGK (any lattice) and D3Q19 MRT take the streamed form; D2Q9 MRT runs collide_fast and then
-// emits.  For D3Q19 MRT the ghost moments of g = f - feq + Ft/2 come first, from the pair sums
+// D3Q19 (BGK and MRT), whose pair kernels are bound by registers, takes the streamed form;
+// D2Q9 runs collide_fast and then emits.  For D3Q19 MRT the ghost moments of g = f - feq + Ft/2 come first, from the pair sums
 // of the stored values and closed forms for the moments of feq and Ft, so no per-population g
 // is kept.  With v = j - F/2 (= rho u - F) and P_a = u_a v_a, the rows of the
 // d'Humieres et al. (2002) basis applied to the equilibrium and the Guo term of Sec. II give
@@ -370,7 +370,7 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
 // where h is the stored value (f, or f - w rho_ref with the shift) and drho = sum_i h_i.
 template <class L, int MRT, bool SHIFT, class T, class Emit>
 __device__ __forceinline__ void collide_emit(const KParams &p, T *f, const T F[3], Emit &&emit) {
-    if constexpr (MRT && !std::is_same<L, D3Q19>::value) {
+    if constexpr (!std::is_same<L, D3Q19>::value) {
         collide_fast<L, MRT, SHIFT, T>(p, f, F);
         Unroll<0, L::Q>::run([&](auto ic) { emit(ic, f[decltype(ic)::value]); });
     } else {
