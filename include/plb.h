@@ -147,7 +147,10 @@ void plb_destroy(plb_t *h);
 
 /* f_i = f_i^eq(rho0, u0) (Eq. Single_Phase_EDF) on every cell; time reset to 0.
  * rho0: host FP64 [N]; u0: host FP64 [d * N] or NULL (u = 0).  Pinned host memory makes
- * the copies asynchronous.  Errors: PLB_EINVAL (non-positive / non-finite rho0), PLB_ECUDA. */
+ * the uploads asynchronous; the call synchronises the stream once at the end, because the
+ * values are checked on the device as they are read.  Errors: PLB_EINVAL (a non-positive or
+ * non-finite rho0, or a non-finite u0; the message names the first such index, and the
+ * populations are undefined until the next successful plb_init), PLB_ECUDA. */
 int plb_init(plb_t *h, const double *rho0, const double *u0);
 
 /* As plb_init, then the populations become f^eq(rho0, u0 - F/(2 rho0)) (Eq. Single_Phase_EDF),

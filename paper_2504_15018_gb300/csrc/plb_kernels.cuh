@@ -38,7 +38,14 @@ __device__ __forceinline__ bool cell_coords(const KParams &p, long long s, int &
 }
 
 // ------------------------------------------------------------ init (a1)
-// f_i = f_i^eq(rho0, u0) in natural layout, for cells [c0, c0 + cn).
+// Records an invalid initial value: FLAG_BAD_INPUT and the smallest such index in `slot`.
+__device__ __forceinline__ void bad_input(const KParams &p, int slot, long long idx) {
+    atomicOr(p.flags, FLAG_BAD_INPUT);
+    atomicMin(reinterpret_cast<unsigned long long *>(p.flags + slot), (unsigned long long)idx);
+}
+
+// f_i = f_i^eq(rho0, u0) in natural layout, for cells [c0, c0 + cn).  A rho0 that is not a
+// positive finite number, or a non-finite u0 component, is recorded (bad_input).
 template <class L, class S>
 __global__ void k_init(KParams p, S *__restrict__ A, const double *__restrict__ rho0, const double *__restrict__ u0,
                        long long c0, long long cn, int has_u) {
@@ -46,10 +53,16 @@ __global__ void k_init(KParams p, S *__restrict__ A, const double *__restrict__ 
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= cn) return;
     const long long s = c0 + k;
-    const T rho = (T)rho0[k];
+    const double r0 = rho0[k];
+    if (!(r0 > 0.0) || !(r0 < INFINITY)) bad_input(p, FLAG_SLOT_RHO, s);
+    const T rho = (T)r0;
     T u[3] = {0, 0, 0};
     if (has_u)
-        for (int a = 0; a < L::D; ++a) u[a] = (T)u0[a * cn + k];
+        for (int a = 0; a < L::D; ++a) {
+            const double ua = u0[a * cn + k];
+            if (!(fabs(ua) < INFINITY)) bad_input(p, FLAG_SLOT_U, a * p.n + s);
+            u[a] = (T)ua;
+        }
     const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T rref = phys<T>(p).rho_ref;
     Unroll<0, L::Q>::run([&](auto ic) {

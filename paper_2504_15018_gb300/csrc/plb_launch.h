@@ -5,7 +5,10 @@
 
 namespace plb {
 
-enum : unsigned { FLAG_PSI_DOMAIN = 1u, FLAG_NONFINITE = 2u };
+enum : unsigned { FLAG_PSI_DOMAIN = 1u, FLAG_NONFINITE = 2u, FLAG_BAD_INPUT = 4u };
+// Device flag area of a lattice (64 bytes): word 0 holds the FLAG_* bits; the 8-byte slots
+// at words 2 and 4 hold the first invalid rho0 and u0 index k_init met (all ones if none).
+enum : int { FLAG_SLOT_RHO = 2, FLAG_SLOT_U = 4 };
 
 // Physical parameters in the arithmetic precision of a kernel (FP64 and FP32 copies are
 // both filled on the host, so no kernel converts a double per thread).

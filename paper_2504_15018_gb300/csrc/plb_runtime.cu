@@ -107,6 +107,14 @@ void *pops_ptr(plb_t *h) { return h->pops; }
 void *psi_ptr(plb_t *h) { return h->psi; }
 double *staging_ptr(plb_t *h) { return h->staging; }
 
+// Cells per staging chunk for a transfer of `need` FP64 values per cell (the staging area
+// holds chunk x max(Q, D + 2) values).
+long long stage_cells(const plb::Layout &L, int need) {
+    const long long per_cell = L.Q > L.D + 2 ? L.Q : L.D + 2;
+    const long long c = L.chunk * per_cell / need;
+    return c < L.n ? c : L.n;
+}
+
 int check_launch() {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PLB_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -380,13 +388,12 @@ int plb_init_physical(plb_t *h, const double *rho0, const double *u0) {
 int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
     if (!h || !rho0) return fail(PLB_EINVAL, "NULL argument");
     const long long n = h->lay.n;
-    for (long long s = 0; s < n; ++s)
-        if (!(rho0[s] > 0.0) || !std::isfinite(rho0[s])) return fail(PLB_EINVAL, "rho0[%lld] is not a positive number", s);
-    if (u0)
-        for (long long s = 0; s < (long long)h->lay.D * n; ++s)
-            if (!std::isfinite(u0[s])) return fail(PLB_EINVAL, "u0[%lld] is not finite", s);
+    // rho0 and u0 are checked on the device as k_init reads them (a host scan of 33 M values
+    // costs tens of milliseconds): flags cleared, first-invalid-index slots set to all ones
+    PLB_CUDA(cudaMemsetAsync(h->kp.flags, 0, 64, h->stream));
+    PLB_CUDA(cudaMemsetAsync(h->kp.flags + plb::FLAG_SLOT_RHO, 0xff, 16, h->stream));
     double *stg = staging_ptr(h);
-    const long long chunk = h->lay.chunk;
+    const long long chunk = stage_cells(h->lay, 1 + (u0 ? h->lay.D : 0));
     for (long long c0 = 0; c0 < n; c0 += chunk) {
         const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
         PLB_CUDA(cudaMemcpyAsync(stg, rho0 + c0, cn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -398,9 +405,16 @@ int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
         int st = check_launch();
         if (st) return st;
     }
-    PLB_CUDA(cudaMemsetAsync(h->kp.flags, 0, 64, h->stream));
+    unsigned long long w[3];        // flag word, first invalid rho0 index, first invalid u0 index
+    PLB_CUDA(cudaMemcpyAsync(w, h->kp.flags, sizeof(w), cudaMemcpyDeviceToHost, h->stream));
+    PLB_CUDA(cudaStreamSynchronize(h->stream));
     h->t = 0;
     h->odd = 0;
+    if ((unsigned)w[0] & plb::FLAG_BAD_INPUT) {
+        PLB_CUDA(cudaMemsetAsync(h->kp.flags, 0, 64, h->stream));
+        if (w[1] != ~0ull) return fail(PLB_EINVAL, "rho0[%lld] is not a positive number", (long long)w[1]);
+        return fail(PLB_EINVAL, "u0[%lld] is not finite", (long long)w[2]);
+    }
     return PLB_OK;
 }
 
@@ -493,8 +507,8 @@ int plb_status(plb_t *h) {
 int plb_moments(plb_t *h, double *rho, double *u, double *p) {
     if (!h) return fail(PLB_EINVAL, "NULL handle");
     h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
-    const long long n = h->lay.n, chunk = h->lay.chunk;
     const int D = h->lay.D;
+    const long long n = h->lay.n, chunk = stage_cells(h->lay, D + 2);
     double *stg = staging_ptr(h);
     for (long long c0 = 0; c0 < n; c0 += chunk) {
         const long long cn = (n - c0) < chunk ? (n - c0) : chunk;

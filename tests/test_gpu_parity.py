@@ -216,6 +216,42 @@ def test_psi_domain_and_invalid_inputs_are_reported():
     lat.status()
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_init_reports_the_first_invalid_value(precision):
+    """rho0 and u0 are checked on the device as plb_init reads them, over staging chunks of up
+    to 2^18 x 19 cells: the error names the first invalid index (rho0 before u0), and a
+    later valid plb_init gives the same populations as a lattice never given bad input."""
+    import paper_2504_15018_gb300 as plb
+    dims = (2 * 640, 640, 1)                       # 819,200 cells: several chunks with u0
+    n = dims[0] * dims[1]
+    rv, rl, _ = maxwell(0.8)
+    case = dict(lattice=0, dims=dims, precision=precision)
+    rng = np.random.default_rng(5)
+    rho = rv * rng.uniform(1.0, 1.02, n)            # vapour with small noise: stable for a few steps
+    u0 = rng.uniform(-0.01, 0.01, (2, n))
+    lat = make_lattice(case, rv, rl)
+    for bad_rho, bad_u, want in (({700_001: -1.0, 812_345: np.nan}, {}, "rho0[700001]"),
+                                 ({5: 0.0}, {(1, 3): np.inf}, "rho0[5]"),
+                                 ({}, {(1, 9): np.nan, (0, 800_000): -np.inf}, f"u0[{800_000}]"),
+                                 ({n - 1: np.inf}, {}, f"rho0[{n - 1}]")):
+        r, u = rho.copy(), u0.copy()
+        for k, v in bad_rho.items():
+            r[k] = v
+        for (a, k), v in bad_u.items():
+            u[a, k] = v
+        with pytest.raises(plb.PlbError) as e:
+            lat.init(r, u)
+        assert e.value.code == plb.PLB_EINVAL
+        assert want in str(e.value), str(e.value)
+    lat.init(rho, u0)
+    lat.step(3)
+    lat.status()
+    ref = make_lattice(case, rv, rl)
+    ref.init(rho, u0)
+    ref.step(3)
+    assert np.array_equal(lat.populations(), ref.populations())
+
+
 @pytest.mark.parametrize("name", ["d2q9_bgk_periodic_droplet", "d3q19_mrt_walls_slab", "d3q19_mrt_periodic_droplet_u0"])
 def test_init_physical_matches_the_balanced_oracle_start(name):
     """plb_init_physical: f^eq(rho0, u0 - F/(2 rho0)) against the same start built from the
