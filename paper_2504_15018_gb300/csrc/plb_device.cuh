@@ -140,6 +140,26 @@ struct LdCoherent {
     template <class U> __device__ __forceinline__ static U ld(const U *a) { return __ldcg(a); }
     template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldcg(a); }
 };
+// LdKeep: loads of data the same kernel reads again shortly (the single-pass kernel reads a
+// plane's populations for psi, then once more a plane later for the collision): L2
+// evict-last priority through a createpolicy cache hint.
+struct LdKeep {
+    __device__ __forceinline__ static unsigned ld(const unsigned *a) {
+        unsigned v;
+        asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+            "ld.global.L2::cache_hint.b32 %0, [%1], pol;\n\t}"
+            : "=r"(v) : "l"(a));
+        return v;
+    }
+    __device__ __forceinline__ static float2 ld(const float2 *a) {
+        float2 v;
+        asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+            "ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], pol;\n\t}"
+            : "=f"(v.x), "=f"(v.y) : "l"(a));
+        return v;
+    }
+    template <class U> __device__ __forceinline__ static U ro(const U *a) { return __ldg(a); }
+};
 // LdBatch: the persistent batch kernel after a grid barrier.  The barrier is a release /
 // acquire pattern at GPU scope (atomic arrival and __threadfence on both sides, then a block
 // barrier), so ordinary L1-cached loads issued after it observe the other blocks' writes.

@@ -17,6 +17,10 @@
 #pragma once
 #include "plb_pair.cuh"
 
+#ifndef PLB_FUSED_PSI_POL
+#define PLB_FUSED_PSI_POL LdKeep
+#endif
+
 namespace plb {
 
 template <class L> struct FusedTile {
@@ -56,7 +60,7 @@ __device__ __forceinline__ void fused_psi_plane(const KParams &p, const Planes<S
         f2 f[L::Q];
         Unroll<0, L::Q>::run([&](auto ic) {
             constexpr int i = decltype(ic)::value;
-            f[i] = PairIO<S>::template ld2<LdStream>(A.p[i] + s0);
+            f[i] = PairIO<S>::template ld2<PLB_FUSED_PSI_POL>(A.p[i] + s0);
         });
         f2 rho = f[0];
 #pragma unroll
