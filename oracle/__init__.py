@@ -17,9 +17,11 @@ Parity status per function (see the tests that pin each one):
   - orc_run: pinned by mass / momentum balance, shear-wave decay (nu = (tau-1/2)/3),
     the parabolic Poiseuille profile between bounce-back walls, MRT == BGK when all
     rates equal 1/tau, and planar-interface coexistence at the Maxwell densities.
-  - MRT ghost-moment rates: parity unpinned (the paper gives no values).
+  - MRT rates: inputs without a paper value; their placement is pinned by each basis mode
+    of a uniform lattice relaxing as (1 - s_k)^n with the other moments at equilibrium.
   - Wetting walls (wall_rho): not in the paper; pinned by a uniform state at the wall density
-    staying at rest, by the mirror-rule limit and by the order of contact angles.
+    staying at rest, by the mirror-rule limit and by the order of contact angles.  The
+    contact angle value itself: parity unpinned (no closed form for this scheme).
 """
 from __future__ import annotations
 

@@ -7,7 +7,8 @@ wrong index or weight, transposed operand):
   - the eps / kappa force terms against the divergence of Eq. New_Pressure_Tensor;
   - mass conservation, momentum balance, Newton's third law of F^SC;
   - shear-wave decay at nu = (tau - 1/2)/3, Poiseuille flow between bounce-back walls;
-  - MRT with all rates 1/tau is BGK; independence of G < 0;
+  - MRT with all rates 1/tau is BGK; each MRT mode relaxes at its own rate; independence
+    of G < 0;
   - planar coexistence at the mechanical-stability densities and second-order
     convergence to the App. A profile under diffusive refinement.
 """
@@ -286,6 +287,39 @@ def test_mrt_with_uniform_rates_is_bgk():
         f = oracle.init(Pb, rho)
         a, b = oracle.run(Pb, f, 40), oracle.run(Pm, f, 40)
         assert np.abs(a - b).max() < 1e-12
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_mrt_modes_relax_at_their_own_rates(lattice):
+    """On a uniform periodic lattice (no force; streaming leaves it uniform) a perturbation
+    along one row k of the MRT basis decays as (1 - s_k)^n while every other moment stays at
+    equilibrium: each rate acts on its own moment (all five ghost rates differ, so a swapped
+    or misplaced rate fails), the stress moments relax with 1/tau, rho and j are conserved."""
+    dims = (4, 4, 1) if lattice == oracle.D2Q9 else (4, 4, 4)
+    tau = 0.8
+    r = dict(s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=0.9, s_m=1.98)
+    P = _grid_params(lattice, dims, tau=tau, mrt=True, rates=r)
+    M, Minv = oracle.mrt_matrix(lattice)
+    q = M.shape[0]
+    if lattice == oracle.D2Q9:        # rho, e, eps, jx, qx, jy, qy, pxx, pxy
+        rate = {1: r["s_e"], 2: r["s_eps"], 4: r["s_q"], 6: r["s_q"], 7: 1 / tau, 8: 1 / tau}
+        conserved = (0, 3, 5)
+    else:                             # rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx, my, mz
+        rate = {1: r["s_e"], 2: r["s_eps"], 4: r["s_q"], 6: r["s_q"], 8: r["s_q"], 9: 1 / tau, 10: r["s_pi"],
+                11: 1 / tau, 12: r["s_pi"], 13: 1 / tau, 14: 1 / tau, 15: 1 / tau, 16: r["s_m"], 17: r["s_m"],
+                18: r["s_m"]}
+        conserved = (0, 3, 5, 7)
+    assert sorted(list(rate) + list(conserved)) == list(range(q))
+    feq = oracle.feq(lattice, 1.3, np.zeros(3))
+    meq = M @ feq
+    delta = 1e-3
+    for k, s_k in rate.items():
+        f = np.tile(feq + delta * Minv[:, k], (oracle.ncells(P), 1))       # m = m_eq + delta e_k
+        for n in (1, 3):
+            dm = oracle.run(P, f, n) @ M.T - meq
+            want = np.zeros(q)
+            want[k] = delta * (1.0 - s_k) ** n
+            assert np.abs(dm - want).max() < 1e-13, (k, n, dm[0], want)
 
 
 def test_dynamics_independent_of_G():
