@@ -18,7 +18,8 @@ Parity status per function (see the tests that pin each one):
     the parabolic Poiseuille profile between bounce-back walls, MRT == BGK when all
     rates equal 1/tau, and planar-interface coexistence at the Maxwell densities.
   - MRT rates: inputs without a paper value; their placement is pinned by each basis mode
-    of a uniform lattice relaxing as (1 - s_k)^n with the other moments at equilibrium.
+    of a uniform lattice relaxing as (1 - s_k)^n with the other moments at equilibrium, and
+    by Poiseuille flow between bounce-back walls being exact at Lambda = 3/16.
   - Wetting walls (wall_rho): not in the paper; pinned by a uniform state at the wall density
     staying at rest, by the mirror-rule limit and by the order of contact angles.  The
     contact angle value itself: parity unpinned (no closed form for this scheme).

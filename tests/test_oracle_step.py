@@ -7,8 +7,8 @@ wrong index or weight, transposed operand):
   - the eps / kappa force terms against the divergence of Eq. New_Pressure_Tensor;
   - mass conservation, momentum balance, Newton's third law of F^SC;
   - shear-wave decay at nu = (tau - 1/2)/3, Poiseuille flow between bounce-back walls;
-  - MRT with all rates 1/tau is BGK; each MRT mode relaxes at its own rate; independence
-    of G < 0;
+  - MRT with all rates 1/tau is BGK; each MRT mode relaxes at its own rate; MRT Poiseuille
+    flow exact at Lambda = 3/16; independence of G < 0;
   - planar coexistence at the mechanical-stability densities and second-order
     convergence to the App. A profile under diffusive refinement.
 """
@@ -320,6 +320,33 @@ def test_mrt_modes_relax_at_their_own_rates(lattice):
             want = np.zeros(q)
             want[k] = delta * (1.0 - s_k) ** n
             assert np.abs(dm - want).max() < 1e-13, (k, n, dm[0], want)
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+def test_mrt_poiseuille_is_exact_at_lambda_3_16(lattice):
+    """Body-force Poiseuille flow between halfway bounce-back walls: with the odd (q, m) rates
+    tied to the shear rate by Lambda = (1/s_nu - 1/2)(1/s_q - 1/2) = 3/16, the steady MRT
+    profile is the parabola with walls exactly half a cell outside the fluid (a known exact
+    property of two-relaxation-time collisions with bounce-back); at Lambda = 1/4 the walls
+    slip by the known O(1/H^2) amount.  Pins the MRT Guo forcing, the odd-moment rates and the
+    bounce-back together."""
+    dims = (4, 16, 1) if lattice == oracle.D2Q9 else (4, 16, 4)
+    H, tau, F, rho0 = dims[1], 0.8, 1e-6, 0.3
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(H)
+    ana = F / (2 * rho0 * nu) * (y + 0.5) * (H - 0.5 - y)
+    dev = {}
+    for lam in (3 / 16, 1 / 4):
+        s_q = 1.0 / (0.5 + lam / (tau - 0.5))
+        P = _grid_params(lattice, dims, wall_y=True, tau=tau, mrt=True, fext=(F, 0, 0),
+                         rates=dict(s_e=1.19, s_eps=1.4, s_q=s_q, s_pi=1.2, s_m=s_q))
+        n = oracle.ncells(P)
+        f = oracle.run(P, oracle.init(P, np.full(n, rho0)), 8000)
+        _, u, _ = oracle.moments(P, f)
+        ux = np.asarray(u).reshape(-1, n)[0].reshape(dims[2], H, dims[0])[0, :, 0]
+        dev[lam] = np.abs(ux - ana).max() / ana.max()
+    assert dev[3 / 16] < 1e-7, dev
+    assert dev[1 / 4] > 1e-4, dev
 
 
 def test_dynamics_independent_of_G():
