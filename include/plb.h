@@ -28,6 +28,8 @@
  *     reported by plb_velocity_set().
  *   - Every function returns a PLB_* status; no exception crosses the ABI.
  *     plb_last_error() gives a message for the last failure on the calling thread.
+ *     A NULL handle gives PLB_EINVAL before any device work (the few functions that
+ *     return a value instead say what they return for it; the destroy calls ignore it).
  *   - The caller owns the device workspace and the CUDA stream; the library never
  *     allocates device memory.  A handle is not thread-safe; use one stream per handle.
  *   - Device work is enqueued on the handle's stream.  Functions that return host
@@ -177,7 +179,7 @@ int plb_step_timed(plb_t *h, int n, double ms[2]);
  * met such a cell since creation or the last plb_init, else PLB_OK. */
 int plb_status(plb_t *h);
 
-/* Number of steps since plb_init. */
+/* Number of steps since plb_init; -1 for a NULL handle. */
 long long plb_time(const plb_t *h);
 
 /* Macroscopic fields of the current state: rho (Eq. Density), u with the F/2 shift
@@ -197,7 +199,8 @@ int plb_get_populations(plb_t *h, double *f);
 int plb_set_populations(plb_t *h, const double *f);
 
 /* Raw checkpoint of the population store and the step counter (bit-exact restart).
- * plb_state_bytes gives the size; get/set return PLB_ENOMEM if bytes is too small. */
+ * plb_state_bytes gives the size (0 for a NULL handle); get/set return PLB_ENOMEM if bytes
+ * is too small. */
 size_t plb_state_bytes(const plb_t *h);
 int plb_get_state(plb_t *h, void *host_buf, size_t bytes);
 int plb_set_state(plb_t *h, const void *host_buf, size_t bytes);
@@ -244,7 +247,7 @@ void plb_batch_destroy(plb_batch_t *b);
 
 /* Instance k as a read-only lattice handle for plb_moments, plb_reduce, plb_get_populations,
  * plb_get_state, plb_status and plb_time (plb_step / plb_init / plb_set_* refuse it; do not
- * destroy it).  NULL for a bad index. */
+ * destroy it).  NULL for a NULL batch or a bad index. */
 plb_t *plb_batch_instance(plb_batch_t *b, int k);
 
 /* f = f^eq(rho0, u0) on instance k (as plb_init); plb_batch_init_physical as plb_init_physical. */
@@ -277,7 +280,7 @@ int plb_batch_autotune(plb_batch_t *b, int steps_per_candidate, int *tile_cells,
  * plb_batch_status reports PLB_ETIMEOUT.  Nothing faults or hangs. */
 int plb_batch_withhold_arrivals(plb_batch_t *b, unsigned count);
 
-/* Steps taken by the batch. */
+/* Steps taken by the batch; -1 for a NULL batch. */
 long long plb_batch_time(const plb_batch_t *b);
 
 /* Allocation-free stepping, for callers that cannot allocate device memory: a plugin

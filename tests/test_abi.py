@@ -153,3 +153,62 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+NULL_HANDLE_CALLS = r"""
+import ctypes, json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import paper_2504_15018_gb300 as plb
+L = plb.lib()
+buf = np.zeros(64)
+dp = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+calls = {
+    "plb_init": lambda: L.plb_init(None, dp, None),
+    "plb_init_physical": lambda: L.plb_init_physical(None, dp, None),
+    "plb_step": lambda: L.plb_step(None, 1),
+    "plb_step_timed": lambda: L.plb_step_timed(None, 1, dp),
+    "plb_status": lambda: L.plb_status(None),
+    "plb_time": lambda: L.plb_time(None),
+    "plb_moments": lambda: L.plb_moments(None, dp, None, None),
+    "plb_reduce": lambda: L.plb_reduce(None, 0, None, None, dp),
+    "plb_get_populations": lambda: L.plb_get_populations(None, dp),
+    "plb_set_populations": lambda: L.plb_set_populations(None, dp),
+    "plb_state_bytes": lambda: L.plb_state_bytes(None),
+    "plb_get_state": lambda: L.plb_get_state(None, None, 0),
+    "plb_set_state": lambda: L.plb_set_state(None, None, 0),
+    "plb_destroy": lambda: L.plb_destroy(None),
+    "plb_batch_instance": lambda: L.plb_batch_instance(None, 0),
+    "plb_batch_init": lambda: L.plb_batch_init(None, 0, dp, None),
+    "plb_batch_init_physical": lambda: L.plb_batch_init_physical(None, 0, dp, None),
+    "plb_batch_step": lambda: L.plb_batch_step(None, 1),
+    "plb_batch_status": lambda: L.plb_batch_status(None),
+    "plb_batch_reset_error": lambda: L.plb_batch_reset_error(None),
+    "plb_batch_configure": lambda: L.plb_batch_configure(None, 0, 0, 0),
+    "plb_batch_autotune": lambda: L.plb_batch_autotune(None, 1, None, None, None),
+    "plb_batch_withhold_arrivals": lambda: L.plb_batch_withhold_arrivals(None, 1),
+    "plb_batch_time": lambda: L.plb_batch_time(None),
+    "plb_batch_destroy": lambda: L.plb_batch_destroy(None),
+}
+print(json.dumps({k: f() for k, f in calls.items()}))
+"""
+
+
+def test_null_handles_are_refused_before_any_device_work(L, tmp_path):
+    """Every entry point that takes a lattice or batch handle, given NULL, returns
+    PLB_EINVAL (or its documented value: -1 steps, 0 bytes, a NULL view) without touching
+    the device; run in a child process so that a crash fails this test only."""
+    import json
+    import subprocess
+    import sys
+    script = tmp_path / "null_calls.py"
+    script.write_text(NULL_HANDLE_CALLS)
+    r = subprocess.run([sys.executable, str(script), ROOT], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = json.loads(r.stdout.strip().splitlines()[-1])
+    value_returning = {"plb_time": -1, "plb_batch_time": -1, "plb_state_bytes": 0,
+                       "plb_batch_instance": None, "plb_destroy": None, "plb_batch_destroy": None}
+    handle_funcs = [n for n in declared_functions() if n in got]
+    assert len(handle_funcs) == len(got)
+    for name, v in got.items():
+        assert v == value_returning.get(name, plb.PLB_EINVAL), (name, v)
