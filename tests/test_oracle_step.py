@@ -6,7 +6,8 @@ wrong index or weight, transposed operand):
   - M^(1), M^(2) exact on quadratic psi; F^SC = -G psi grad psi on linear psi;
   - the eps / kappa force terms against the divergence of Eq. New_Pressure_Tensor;
   - mass conservation, momentum balance, Newton's third law of F^SC;
-  - shear-wave decay at nu = (tau - 1/2)/3, Poiseuille flow between bounce-back walls;
+  - shear-wave decay at nu = (tau - 1/2)/3, also with tau(rho) interpolated and clamped;
+    Poiseuille flow between bounce-back walls;
   - MRT with all rates 1/tau is BGK; each MRT mode relaxes at its own rate; MRT Poiseuille
     flow exact at Lambda = 3/16; independence of G < 0;
   - planar coexistence at the mechanical-stability densities and second-order
@@ -255,6 +256,26 @@ def test_shear_wave_decay(lattice, mrt, tau):
     steps = int(1.15 / (nu * k * k))
     f = oracle.init(P, np.full(n, 7.5), u0)
     _, u, _ = oracle.moments(P, oracle.run(P, f, steps))
+    amp = 2.0 / n * (u[0] * np.sin(k * y)).sum()
+    assert -math.log(amp / U) / (nu * k * k * steps) == pytest.approx(1.0, abs=3e-3)
+
+
+@pytest.mark.parametrize("tau_rho,want_tau", [((7.0, 8.0), 0.8), ((5.0, 7.0), 1.0), ((8.0, 9.0), 0.6)])
+def test_shear_wave_decay_follows_tau_of_rho(tau_rho, want_tau):
+    """tau(rho) of Sec. VI in the dynamics: a shear wave on a uniform liquid at rho = 7.5, with
+    tau_v = 0.6 at rho_v and tau_l = 1.0 at rho_l, decays at nu = (tau(7.5) - 1/2)/3 where
+    tau is interpolated linearly between (rho_v, rho_l) = tau_rho and clamped outside it."""
+    n = 64
+    dims = (1, n, 1)
+    P = _grid_params(oracle.D2Q9, dims, tau=1.0, tau_v=0.6, tau_rho=tau_rho)
+    y = np.arange(n)
+    k = 2 * np.pi / n
+    U = 1e-4
+    u0 = np.zeros((2, n))
+    u0[0] = U * np.sin(k * y)
+    nu = (want_tau - 0.5) / 3.0
+    steps = int(1.15 / (nu * k * k))
+    _, u, _ = oracle.moments(P, oracle.run(P, oracle.init(P, np.full(n, 7.5), u0), steps))
     amp = 2.0 / n * (u[0] * np.sin(k * y)).sum()
     assert -math.log(amp / U) / (nu * k * k * steps) == pytest.approx(1.0, abs=3e-3)
 
