@@ -208,11 +208,16 @@ __global__ void __launch_bounds__(256) k_reduce(KParams p, const S *__restrict__
         load_pops<L, S>(p, A, x, y, z, nb, s, odd != 0, f);
         double rho = 0, j[3] = {0, 0, 0};
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            rho += (double)f[i];
-            j[0] += (double)(L::cx(i) * f[i]);
-            j[1] += (double)(L::cy(i) * f[i]);
-            j[2] += (double)(L::cz(i) * f[i]);
+        for (int i = 0; i < L::Q; ++i) rho += (double)f[i];
+        if (what >= 1 && what <= 4) {
+            // momentum only where it is used (GB300's FP64 rate is low); terms with a
+            // zero velocity component add exactly 0 and are skipped
+            Unroll<0, L::Q>::run([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if (L::cx(i) != 0) j[0] += (double)(L::cx(i) * f[i]);
+                if (L::cy(i) != 0) j[1] += (double)(L::cy(i) * f[i]);
+                if (L::cz(i) != 0) j[2] += (double)(L::cz(i) * f[i]);
+            });
         }
         if (what == 0 || what == 5) {
             acc[0] += rho;
