@@ -165,7 +165,7 @@ KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_kernels.
 
 def kernel_source_sha():
     """Hash of the files that hold the step kernels' device code (k_psi_pair, k_collide_pair,
-    k_fused_pair and everything they inline)."""
+    k_fused_pair and everything they inline) and their launch shapes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_15018_gb300", "csrc")
     for f in KERNEL_SOURCES:
