@@ -300,7 +300,6 @@ __global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float 
 #define PLB_PAIR_MAXREG 112
 #endif
 
-
 template <class L, class S, int MRT, bool ODD, bool WALL, class Pol = LdStream, bool SR = false>
 __device__ __forceinline__ void collide_pair_body(const KParams &p, const Planes<S> &A, const float *__restrict__ psi,
                                                   const GeoPair &g, unsigned salt = 0) {

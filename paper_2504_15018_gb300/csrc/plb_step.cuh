@@ -359,13 +359,14 @@ __device__ __forceinline__ void collide_fast(const KParams &p, T *f, const T F[3
 // value of population decltype(ic)::value as soon as it is final, so that a pair's registers
 // are free once it is stored.  Equal to collide_fast in exact arithmetic (rounding differs).
 // D3Q19 (BGK and MRT), whose pair kernels are bound by registers, takes the streamed form;
-// D2Q9 runs collide_fast and then emits.  For D3Q19 MRT the ghost moments of g = f - feq + Ft/2 come first, from the pair sums
-// of the stored values and closed forms for the moments of feq and Ft, so no per-population g
-// is kept.  With v = j - F/2 (= rho u - F) and P_a = u_a v_a, the rows of the
+// D2Q9 runs collide_fast and then emits.  For D3Q19 MRT the ghost moments of
+// g = f - feq + Ft/2 come first, from the pair sums of the stored values and closed forms for
+// the moments of feq and Ft, so no per-population g is kept.  With v = j - F/2 (= rho u - F) and P_a = u_a v_a, the rows of the
 // d'Humieres et al. (2002) basis applied to the equilibrium and the Guo term of Sec. II give
 // (sums over the D3Q19 velocities):
 //   m_e(g)   = m_e(h)   + 11 drho - 19 u.v        m_eps(g) = m_eps(h) - 3 drho + 5.5 u.v
 //   m_pxx(g) = m_pxx(h) + P_x - (P_y + P_z) / 2   m_pww(g) = m_pww(h) + (P_y - P_z) / 2
+//   (m_pxx, m_pww: the fourth-order 3 pi_xx and pi_ww rows, as in ghosts_d3q19)
 //   m_q(g)   = m_q(h)   + (2/3) j                 m_m(g)   = m_m(h)
 // where h is the stored value (f, or f - w rho_ref with the shift) and drho = sum_i h_i.
 template <class L, int MRT, bool SHIFT, class T, class Emit>
