@@ -78,11 +78,21 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def build_variant(path: str, mutant: int) -> str:
+    """Compile ``lbm.c`` with the planted mistake ``ORC_MUTANT=mutant`` into ``path``
+    (tests only: the pins must fail on every such build)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-fopenmp", f"-DORC_MUTANT={int(mutant)}", _SRC, "-o", path, "-lm"]
+    subprocess.run(cmd, check=True)
+    return path
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # ORC_LIB_OVERRIDE: a build_variant() library, set only by the planted-mistake tests
+            L = ctypes.CDLL(os.environ.get("ORC_LIB_OVERRIDE") or build())
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(OrcParams)
             L.orc_velocity_set.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]

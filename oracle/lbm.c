@@ -52,6 +52,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* ORC_MUTANT (tests only, default 0): builds with a planted mistake, one per value, so that
+ * tests/test_oracle_mutants.py can check that some pin fails on each.  0 is the oracle. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+
 #define ORC_OK 0
 #define ORC_EINVAL 1
 #define ORC_EPSI_DOMAIN 2
@@ -178,7 +184,11 @@ void orc_feq(int lattice, double rho, const double *u, double *feq) {
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
                 quad += (c[a] * c[b] - CS2 * (a == b)) * u[a] * u[b];
+#if ORC_MUTANT == 1
+        feq[i] = lat_w(lattice, i) * rho * (1.0 + cu / CS2 - quad / (2.0 * CS2 * CS2));
+#else
         feq[i] = lat_w(lattice, i) * rho * (1.0 + cu / CS2 + quad / (2.0 * CS2 * CS2));
+#endif
     }
 }
 
@@ -192,7 +202,11 @@ static void guo_bracket(int lattice, const double *F, const double *u, double *o
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
                 quad += (c[a] * c[b] - CS2 * (a == b)) * F[a] * u[b];
+#if ORC_MUTANT == 2
+        out[i] = lat_w(lattice, i) * (cF / CS2 + 0.0 * quad);
+#else
         out[i] = lat_w(lattice, i) * (cF / CS2 + quad / (CS2 * CS2));
+#endif
     }
 }
 
@@ -273,9 +287,9 @@ static double mrt_rate(const orc_params *P, int k, double tau) {
     switch (k) {
         case 1: return P->s_e;
         case 2: return P->s_eps;
-        case 4: case 6: case 8: return P->s_q;
+        case 4: case 6: case 8: return ORC_MUTANT == 5 ? P->s_m : P->s_q;
         case 10: case 12: return P->s_pi;
-        case 16: case 17: case 18: return P->s_m;
+        case 16: case 17: case 18: return ORC_MUTANT == 5 ? P->s_q : P->s_m;
         case 9: case 11: case 13: case 14: case 15: return 1.0 / tau;
         default: return 1.0 / tau;  /* conserved: rho, jx, jy, jz */
     }
@@ -369,7 +383,11 @@ static void cell_force(const orc_params *P, const double *psi, int x, int y, int
         double pn = psi_neighbour(P, psi, x, y, z, c[i]);
         double w = lat_w(P->lattice, i);
         for (int a = 0; a < 3; ++a) {
+#if ORC_MUTANT == 4
+            M1[a] += w * pn * c[i][a];
+#else
             M1[a] += w * pn * c[i][a] / CS2;
+#endif
             for (int b = 0; b < 3; ++b)
                 M2[3 * a + b] += w * pn * (c[i][a] * c[i][b] - CS2 * (a == b)) / (CS2 * CS2);
         }
@@ -385,8 +403,13 @@ static void cell_force(const orc_params *P, const double *psi, int x, int y, int
         double M1M2 = 0.0;
         for (int b = 0; b < d; ++b) M1M2 += M1[b] * M2[3 * a + b];
         double eps_term = P->eps_printed ? 1.5 * P->eps : -3.0 * P->eps;
+#if ORC_MUTANT == 3
+        double Fint = Fsc - (P->G / 12.0) * (eps_term + 2.0 * P->kappa - 2.0) * M1M2
+                          - (P->G / 6.0) * (P->kappa - 1.0) * M1[a] * trM2;
+#else
         double Fint = Fsc - (P->G / 12.0) * (eps_term + 2.0 * P->kappa - 2.0) * M1M2
                           + (P->G / 6.0) * (P->kappa - 1.0) * M1[a] * trM2;
+#endif
         F[a] = a < d ? Fint + P->fext[a] : 0.0;
     }
 }
@@ -482,7 +505,7 @@ static void collide_cell(const orc_params *P, const double *fc, const double *F,
         }
         double s = mrt_rate(P, k, tau);
         dm[k] = s * mneq;
-        mF[k] = (1.0 - s / 2.0) * mf;
+        mF[k] = (ORC_MUTANT == 6 ? 1.0 - s : 1.0 - s / 2.0) * mf;
     }
     for (int i = 0; i < q; ++i) {
         double corr = 0.0;
@@ -518,7 +541,7 @@ int orc_run(const orc_params *P, double *f, int nsteps) {
                     collide_cell(P, f + s * q, F, fpost, M, Minv);
                     for (int i = 0; i < q; ++i) {
                         int yn = y + c[i][1];
-                        if (P->wall_y && (yn < 0 || yn >= ny)) {
+                        if (P->wall_y && (yn < 0 || (ORC_MUTANT == 7 ? yn > ny : yn >= ny))) {
                             fnew[s * q + opp[i]] = fpost[i];              /* halfway bounce-back */
                         } else {
                             long t = cell_index(P, wrap(x + c[i][0], nx), wrap(yn, ny), wrap(z + c[i][2], nz));
