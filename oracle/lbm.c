@@ -111,7 +111,7 @@ static double lat_omega(int lattice, int i) {
     const int *c = lat_c(lattice)[i];
     int c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
     if (c2 == 0) return 0.0;
-    if (lattice == 0) return c2 == 1 ? 1.0 / 3.0 : 1.0 / 12.0;
+    if (lattice == 0) return c2 == 1 ? 1.0 / 3.0 : (ORC_MUTANT == 10 ? 1.0 / 6.0 : 1.0 / 12.0);
     return c2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
 }
 
@@ -166,7 +166,7 @@ double orc_pressure(const orc_params *P, double rho) {
 /* Eq. Interaction_Potential: psi = sqrt(2 (p - rho/3) / G); p already carries Delta t^2/Delta x^2. */
 static int psi_of_rho(const orc_params *P, double rho, double *psi) {
     if (!(rho > 0.0) || !isfinite(rho)) return ORC_ENONFINITE;
-    double arg = 2.0 * (orc_pressure(P, rho) - rho / 3.0) / P->G;
+    double arg = (ORC_MUTANT == 8 ? 1.0 : 2.0) * (orc_pressure(P, rho) - rho / 3.0) / P->G;
     if (!(arg >= 0.0)) return ORC_EPSI_DOMAIN;
     *psi = sqrt(arg);
     return ORC_OK;
@@ -222,7 +222,7 @@ static double tau_of_rho(const orc_params *P, double rho) {
     if (P->tau_v == P->tau_l) return P->tau_l;
     double wgt = (rho - P->tau_rho_v) / (P->tau_rho_l - P->tau_rho_v);
     if (wgt < 0.0) wgt = 0.0;
-    if (wgt > 1.0) wgt = 1.0;
+    if (wgt > 1.0 && ORC_MUTANT != 9) wgt = 1.0;
     return P->tau_v + wgt * (P->tau_l - P->tau_v);
 }
 

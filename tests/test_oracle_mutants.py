@@ -1,4 +1,4 @@
-"""The oracle's pins are sharp: for each of seven plausible mistakes planted in the oracle
+"""The oracle's pins are sharp: for each of ten plausible mistakes planted in the oracle
 (a separate build of lbm.c with ORC_MUTANT = k; the oracle itself is ORC_MUTANT = 0), the pin
 aimed at it fails, while the same pins pass on an unmutated build made the same way.  Each run
 is a child pytest process that loads the variant through ORC_LIB_OVERRIDE."""
@@ -21,6 +21,10 @@ MUTANTS = {
     5: ("D3Q19 MRT rates s_q and s_m swapped", "test_mrt_modes_relax_at_their_own_rates"),
     6: ("MRT forcing factor 1 - s instead of 1 - s/2", "test_momentum_balance_and_third_law"),
     7: ("upper bounce-back wall off by one row", "test_poiseuille_between_bounce_back_walls"),
+    8: ("psi without the factor 2 of Eq. Interaction_Potential",
+        "test_planar_coexistence_follows_mechanical_stability"),
+    9: ("tau(rho) not clamped above rho_l", "test_shear_wave_decay_follows_tau_of_rho"),
+    10: ("D2Q9 Shan-Chen weight omega(2) = 1/6 instead of 1/12", "test_stencils_exact_on_quadratic_psi"),
 }
 
 
