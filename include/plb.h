@@ -184,23 +184,28 @@ long long plb_time(const plb_t *h);
 
 /* Macroscopic fields of the current state: rho (Eq. Density), u with the F/2 shift
  * (Eq. Momentum), p = p_scale p_EOS(rho).  Host FP64 outputs, each may be NULL:
- * rho [N], u [d * N], p [N].  Synchronises. */
+ * rho [N], u [d * N], p [N].  Synchronises.  Errors: PLB_EINVAL (NULL handle),
+ * PLB_EPSI_DOMAIN / PLB_ENONFINITE (as plb_status), PLB_ECUDA. */
 int plb_moments(plb_t *h, double *rho, double *u, double *p);
 
-/* A reduction over the box lo <= (x, y, z) < hi (NULL = whole lattice), summed in
+/* A reduction over the box lo <= (x, y, z) < hi (clipped to the lattice; NULL = whole), summed in
  * FP64 in a fixed order (deterministic).  out receives 1 value (3 for PLB_MOMENTUM).
- * Synchronises. */
+ * Synchronises.  Errors: PLB_EINVAL (NULL handle or out, unknown reduction, empty box),
+ * PLB_EPSI_DOMAIN / PLB_ENONFINITE (as plb_status), PLB_ECUDA. */
 int plb_reduce(plb_t *h, int what, const int lo[3], const int hi[3], double *out);
 
-/* Current populations f_i(x, t) (pre-collision) as host FP64 [Q * N], direction-major. */
+/* Current populations f_i(x, t) (pre-collision) as host FP64 [Q * N], direction-major.
+ * Errors: PLB_EINVAL (NULL argument), PLB_ECUDA. */
 int plb_get_populations(plb_t *h, double *f);
 
-/* Replaces the populations (host FP64 [Q * N]); keeps the step counter. */
+/* Replaces the populations (host FP64 [Q * N]); keeps the step counter.  Errors:
+ * PLB_EINVAL (NULL argument, or a batch instance view), PLB_ECUDA. */
 int plb_set_populations(plb_t *h, const double *f);
 
 /* Raw checkpoint of the population store and the step counter (bit-exact restart).
  * plb_state_bytes gives the size (0 for a NULL handle); get/set return PLB_ENOMEM if bytes
- * is too small. */
+ * is too small, PLB_EINVAL for a NULL argument (set also for a batch instance view or a
+ * state taken from another lattice), PLB_ECUDA. */
 size_t plb_state_bytes(const plb_t *h);
 int plb_get_state(plb_t *h, void *host_buf, size_t bytes);
 int plb_set_state(plb_t *h, const void *host_buf, size_t bytes);
