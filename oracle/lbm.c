@@ -123,7 +123,12 @@ static int lat_opposite(int lattice, int i) {
     return -1;
 }
 
+/* c_s^2 = 1/3 in lattice units (Eq. VelocitySet).  Its inverse powers are the exact numbers
+ * 1/c_s^2 = 3 and 1/c_s^4 = 9, so the formulas below multiply by them rather than divide by the
+ * rounded FP64 value of 1/3, which would add a rounding the equations do not have. */
 static const double CS2 = 1.0 / 3.0;
+static const double INV_CS2 = 3.0;
+static const double INV_CS4 = 9.0;
 
 int orc_velocity_set(int lattice, int *c_out, double *w_out) {
     if (lattice != 0 && lattice != 1) return -1;
@@ -185,9 +190,9 @@ void orc_feq(int lattice, double rho, const double *u, double *feq) {
             for (int b = 0; b < 3; ++b)
                 quad += (c[a] * c[b] - CS2 * (a == b)) * u[a] * u[b];
 #if ORC_MUTANT == 1
-        feq[i] = lat_w(lattice, i) * rho * (1.0 + cu / CS2 - quad / (2.0 * CS2 * CS2));
+        feq[i] = lat_w(lattice, i) * rho * (1.0 + cu * INV_CS2 - quad * (0.5 * INV_CS4));
 #else
-        feq[i] = lat_w(lattice, i) * rho * (1.0 + cu / CS2 + quad / (2.0 * CS2 * CS2));
+        feq[i] = lat_w(lattice, i) * rho * (1.0 + cu * INV_CS2 + quad * (0.5 * INV_CS4));
 #endif
     }
 }
@@ -203,9 +208,9 @@ static void guo_bracket(int lattice, const double *F, const double *u, double *o
             for (int b = 0; b < 3; ++b)
                 quad += (c[a] * c[b] - CS2 * (a == b)) * F[a] * u[b];
 #if ORC_MUTANT == 2
-        out[i] = lat_w(lattice, i) * (cF / CS2 + 0.0 * quad);
+        out[i] = lat_w(lattice, i) * (cF * INV_CS2 + 0.0 * quad);
 #else
-        out[i] = lat_w(lattice, i) * (cF / CS2 + quad / (CS2 * CS2));
+        out[i] = lat_w(lattice, i) * (cF * INV_CS2 + quad * INV_CS4);
 #endif
     }
 }
@@ -386,10 +391,10 @@ static void cell_force(const orc_params *P, const double *psi, int x, int y, int
 #if ORC_MUTANT == 4
             M1[a] += w * pn * c[i][a];
 #else
-            M1[a] += w * pn * c[i][a] / CS2;
+            M1[a] += w * pn * c[i][a] * INV_CS2;
 #endif
             for (int b = 0; b < 3; ++b)
-                M2[3 * a + b] += w * pn * (c[i][a] * c[i][b] - CS2 * (a == b)) / (CS2 * CS2);
+                M2[3 * a + b] += w * pn * (c[i][a] * c[i][b] - CS2 * (a == b)) * INV_CS4;
         }
         if (i > 0)
             for (int a = 0; a < 3; ++a) sc[a] += lat_omega(P->lattice, i) * pn * c[i][a];
