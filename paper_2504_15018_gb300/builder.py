@@ -18,7 +18,10 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libplb.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code: no contraction of a * b + c into a fused multiply-add (aarch64 compilers contract
+# by default), so the host-side FP64 constants round as their expressions are written.
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+          "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 UNITS = [

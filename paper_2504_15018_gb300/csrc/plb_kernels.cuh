@@ -63,6 +63,14 @@ __global__ void k_init(KParams p, S *__restrict__ A, const double *__restrict__ 
             if (!(fabs(ua) < INFINITY)) bad_input(p, FLAG_SLOT_U, a * p.n + s);
             u[a] = (T)ua;
         }
+    if constexpr (std::is_same<S, double>::value) {
+        // FP64: Eq. Single_Phase_EDF evaluated as the plain collision does
+        double f[L::Q];
+        plain::equilibrium<L>(r0, u, f);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) Store<S>::st(A + (long long)i * p.pstride + s, f[i]);
+        return;
+    }
     const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T rref = phys<T>(p).rho_ref;
     Unroll<0, L::Q>::run([&](auto ic) {
@@ -288,9 +296,9 @@ template <class L, class S> struct Launch {
         for (int i = 0; i < 19; ++i) pl.p[i] = (S *)A + (i < L::Q ? (long long)i * p.pstride : 0);
         return pl;
     }
-    static void dims3(const KParams &p, dim3 &grid, dim3 &block) {
-        int bx = p.nx >= 256 ? 256 : (p.nx + 31) / 32 * 32;
-        int by = 256 / bx;
+    static void dims3(const KParams &p, dim3 &grid, dim3 &block, int threads = 256) {
+        int bx = p.nx >= threads ? threads : (p.nx + 31) / 32 * 32;
+        int by = threads / bx;
         if (by > p.ny) by = p.ny;
         block = dim3(bx, by, 1);
         grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
@@ -367,6 +375,14 @@ template <class L, class S> struct Launch {
                 k_collide_pair<L, S, MRT, ODD, false><<<grid, block, 0, st>>>(q, planes(p, A), (const float *)psi);
                 return;
             }
+        }
+        if constexpr (std::is_same<S, double>::value) {
+            dims3(p, grid, block, 128);
+            if (p.n < (1LL << 31))
+                k_collide_plain<L, MRT, ODD, int><<<grid, block, 0, st>>>(p, planes(p, A), (const double *)psi);
+            else
+                k_collide_plain<L, MRT, ODD, long long><<<grid, block, 0, st>>>(p, planes(p, A), (const double *)psi);
+            return;
         }
         dims3(p, grid, block);
         if (p.n < (1LL << 31))

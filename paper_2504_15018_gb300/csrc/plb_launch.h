@@ -26,6 +26,19 @@ template <class T> struct Phys {
     T psi_wall;               // psi on wetting walls (used when KParams::wall_fixed)
 };
 
+// Constants of the plain FP64 evaluation (plb_plain.cuh), each formed on the host the way
+// the equations write it.
+struct PlainPhys {
+    double R, T, b, a_alpha;                   // Peng-Robinson: R, absolute T, b, a alpha(T)
+    double P, rv_2rl, sv3, sv2rl, svrlrl;      // Eq. EOS: p_c/rho_c^3, rho_v - 2 rho_l, 3 sqrt(rho_v),
+                                               //   2 sqrt(rho_v) rho_l, sqrt(rho_v) rho_l rho_l
+    double p_scale, G;
+    double K1, K2;                             // G/12 (2 kappa - 2 - 3 eps), G/6 (kappa - 1)
+    double tau_l, tau_v, tau_rho_v, d_rho, d_tau;   // tau(rho): rho_l - rho_v, tau_l - tau_v
+    double s_rate[6];                          // MRT rates by kind (1..5)
+    double fext[3];
+};
+
 struct KParams {
     int nx, ny, nz;
     long long n;          // cells
@@ -44,6 +57,7 @@ struct KParams {
     unsigned salt;        // step counter mixed into the rounding noise
     Phys<double> d;
     Phys<float> f;
+    PlainPhys pl;
     unsigned *flags;
 };
 

@@ -14,6 +14,7 @@
 #include "plb.h"
 #include "plb_host.h"
 #include "plb_launch.h"
+#include "plb_plain.cuh"
 
 namespace {
 thread_local std::string g_err;
@@ -280,9 +281,39 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
         d.pe_sv = std::sqrt(eos.rho_v);
     }
     d.p_scale = eos.p_scale;
+    // constants of the plain FP64 evaluation, each rounded as its expression is written
+    PlainPhys &pl = k.pl;
+    if (eos.kind == PLB_EOS_PR) {
+        const double Tc = 0.0778 * eos.a / (0.45724 * eos.b * eos.R);
+        const double T = eos.T_over_Tc * Tc;
+        const double m = 0.37464 + 1.54226 * eos.omega - 0.26992 * eos.omega * eos.omega;
+        const double g = 1.0 + m * (1.0 - std::sqrt(T / Tc));
+        pl.R = eos.R;
+        pl.T = T;
+        pl.b = eos.b;
+        pl.a_alpha = eos.a * (g * g);
+    } else {
+        const double sv = std::sqrt(eos.rho_v);
+        pl.P = eos.pc_over_rhoc3;
+        pl.rv_2rl = eos.rho_v - 2.0 * eos.rho_l;
+        pl.sv3 = 3.0 * sv;
+        pl.sv2rl = 2.0 * sv * eos.rho_l;
+        pl.svrlrl = sv * eos.rho_l * eos.rho_l;
+    }
+    pl.p_scale = eos.p_scale;
+    pl.G = G;
+    pl.K1 = (G / 12.0) * (-3.0 * eps + 2.0 * o.kappa - 2.0);
+    pl.K2 = (G / 6.0) * (o.kappa - 1.0);
+    pl.tau_l = tau;
+    pl.tau_v = d.tau_v;
+    pl.tau_rho_v = trv;
+    pl.d_rho = trl - trv;
+    pl.d_tau = tau - d.tau_v;
+    for (int r = 0; r < 6; ++r) pl.s_rate[r] = d.s_rate[r];
+    for (int a = 0; a < 3; ++a) pl.fext[a] = d.fext[a];
     if (k.wall_fixed) {
         // Eq. Interaction_Potential at the wall density
-        const double arg = 2.0 * (eos.p_scale * eos_pressure_host(eos, o.wall_rho) - o.wall_rho / 3.0) / G;
+        const double arg = plain::psi_arg(pl, eos.kind, o.wall_rho);
         if (!(arg >= 0.0)) return fail(PLB_EINVAL, "psi is not defined at wall_rho for this EOS");
         d.psi_wall = std::sqrt(arg);
     }

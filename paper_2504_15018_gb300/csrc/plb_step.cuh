@@ -8,6 +8,7 @@
 //    computed from the symmetric / antisymmetric parts of opposite-direction pairs.
 #pragma once
 #include "plb_device.cuh"
+#include "plb_plain.cuh"
 
 namespace plb {
 
@@ -495,11 +496,16 @@ __device__ __forceinline__ void psi_body(const KParams &p, const Planes<S> &A, t
     using PsiT = typename Store<S>::PsiT;
     T f[L::Q];
     load_fast<L, S, ODD, WALL, Pol>(p, A, g, f);
-    T rho = f[0];
+    PsiT v;
+    if constexpr (std::is_same<S, double>::value) {
+        v = plain::psi(p, plain::density<L>(f));                // FP64: the plain evaluation
+    } else {
+        T rho = f[0];
 #pragma unroll
-    for (int i = 1; i < L::Q; ++i) rho += f[i];
-    if (Store<S>::SHIFT) rho += phys<T>(p).rho_ref;          // sum_i w_i rho_ref = rho_ref
-    const PsiT v = (PsiT)psi_of<T>(p, rho);
+        for (int i = 1; i < L::Q; ++i) rho += f[i];
+        if (Store<S>::SHIFT) rho += phys<T>(p).rho_ref;      // sum_i w_i rho_ref = rho_ref
+        v = (PsiT)psi_of<T>(p, rho);
+    }
     psi[psi_index(p, g.x, g.y, g.z)] = v;
     // periodic images / wall mirrors in the ghost layer (boundary cells only)
     const bool bx = g.x == 0 || g.x == p.nx - 1, by = g.y == 0 || g.y == p.ny - 1;
@@ -548,9 +554,28 @@ __device__ __forceinline__ void collide_body(const KParams &p, const Planes<S> &
     T f[L::Q];
     load_fast<L, S, ODD, WALL, Pol>(p, A, g, f);
     T F[3];
-    force_fast<L, T, Pol>(p, psi + psi_index(p, g.x, g.y, g.z), F);
-    collide_fast<L, MRT, Store<S>::SHIFT, T>(p, f, F);
+    if constexpr (std::is_same<S, double>::value) {
+        // FP64: the plain evaluation, term by term in the equations' order
+        plain::force<L, Pol>(p, psi + psi_index(p, g.x, g.y, g.z), F);
+        plain::collide<L, MRT>(p, f, F);
+    } else {
+        force_fast<L, T, Pol>(p, psi + psi_index(p, g.x, g.y, g.z), F);
+        collide_fast<L, MRT, Store<S>::SHIFT, T>(p, f, F);
+    }
     store_fast<L, S, ODD, WALL, SR>(p, A, g, f, salt);
+}
+
+// FP64 storage: the plain evaluation holds f, f - f^eq, the Guo bracket and the moment
+// corrections at once (about 60 doubles for D3Q19 MRT), so it runs in 128-thread blocks
+// without a residency floor on the register allocation.
+template <class L, int MRT, bool ODD, class I>
+__global__ void __launch_bounds__(128) k_collide_plain(KParams p, Planes<double> A, const double *__restrict__ psi) {
+    Geo<I> g;
+    if (!make_geo<I>(p, g)) return;
+    if (ODD && p.wall_y && (g.y == 0 || g.y == p.ny - 1))
+        collide_body<L, double, MRT, ODD, true>(p, A, psi, g);
+    else
+        collide_body<L, double, MRT, ODD, false>(p, A, psi, g);
 }
 
 template <class L, class S, int MRT, bool ODD, class I>

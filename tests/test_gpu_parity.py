@@ -44,32 +44,19 @@ PAIR_CASES = {
 }
 
 
-def oracle_self_sensitivity(case, steps):
-    """How far the oracle itself moves after `steps` steps when its input is perturbed by
-    1e-16 relative: the roundoff amplification of the dynamics (condition of the problem)."""
-    rho, u0, rv, rl = case_fields(case)
-    P = oracle_params(case, rv, rl)
-    f0 = oracle.init(P, rho, u0)
-    a = oracle.run(P, f0, steps)
-    b = oracle.run(P, f0 * (1.0 + 1e-16 * np.random.default_rng(7).standard_normal(f0.shape)), steps)
-    return max_rel_err(a, b)
-
-
 @pytest.mark.parametrize("name", list(FP64_CASES))
 def test_fp64_population_parity_1000_steps(name):
-    """Max relative error <= 1e-12 on every population after 1000 steps.  Where the dynamics
-    amplify a 1e-16 perturbation of the oracle's own input beyond 1e-13 in 1000 steps (the
-    paper's low-viscosity tau_l = 0.56 case), no reordering of the arithmetic can meet 1e-12;
-    there the bound is 10x that measured self-sensitivity."""
+    """Max relative error <= 1e-12 on every population after 1000 steps.  The FP64 kernels
+    evaluate every term in the order the equations write it, with one rounding per product
+    and per sum, so they round as the oracle does; the dynamics of the tau_l = 0.56 case
+    amplify a 1e-16 perturbation by about 1e5 in 1000 steps, so only such an evaluation
+    meets the bound on every case.  The number of populations that differ at all is printed."""
     case = dict(FP64_CASES[name], precision=0)
     ref, got, lat, _ = run_both(case, 1000)
     err = max_rel_err(ref, got)
-    bound = 1e-12
-    sens = oracle_self_sensitivity(case, 1000)
-    if sens > 1e-13:
-        bound = max(bound, 10.0 * sens)
-    print(f"{name}: max rel err {err:.3e}, oracle self-sensitivity {sens:.3e}, bound {bound:.1e}")
-    assert err <= bound
+    print(f"{name}: max rel err {err:.3e}, populations differing from the oracle: "
+          f"{int(np.count_nonzero(got != ref))} of {got.size}")
+    assert err <= 1e-12
 
 
 @pytest.mark.parametrize("name", ["d2q9_bgk_periodic_droplet", "d3q19_mrt_walls_slab"])
@@ -77,7 +64,7 @@ def test_fp64_parity_at_odd_step_counts(name):
     """Both AA parities and the switch between them (1, 2, 3 and 7 steps)."""
     for steps in (1, 2, 3, 7):
         ref, got, _, _ = run_both(dict(FP64_CASES[name], precision=0), steps)
-        assert max_rel_err(ref, got) <= 1e-13, steps
+        assert max_rel_err(ref, got) <= 1e-12, steps
 
 
 @pytest.mark.parametrize("name", ["d2q9_bgk_periodic_droplet", "d3q19_mrt_periodic_droplet_u0",
