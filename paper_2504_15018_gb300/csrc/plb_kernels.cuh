@@ -15,7 +15,11 @@
 #ifndef PLB_L2_PREFETCH
 #define PLB_L2_PREFETCH 1
 #endif
-// L2 prefetch distance of the FP32 fused pass in waves of resident blocks.
+// The same for FP16-shifted storage.
+#ifndef PLB_L2_PREFETCH_HALF
+#define PLB_L2_PREFETCH_HALF 0
+#endif
+// L2 prefetch distance of the fused pass in waves of resident blocks.
 #ifndef PLB_PF_WAVES
 #define PLB_PF_WAVES 1
 #endif
@@ -269,6 +273,49 @@ __global__ void __launch_bounds__(256) k_reduce(KParams p, const S *__restrict__
     }
 }
 
+// Total mass of the whole lattice.  In either AA layout every population of every cell sits in
+// exactly one slot of the store, so the mass is the sum of the Q planes over the N cells (plus
+// N rho_ref with the FP16 shift): no coordinates, no neighbour addressing, coalesced loads.
+// FP32 arithmetic: each cell's Q values are summed with an error-free compensated sum (TwoSum),
+// the cell's sum and correction then added in FP64 per thread; FP64 storage sums in FP64.
+// One partial per block in partials[4 * block] (the final pass sums them in block order).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_mass_flat(KParams p, const S *__restrict__ A, double *__restrict__ partials) {
+    using T = typename Store<S>::T;
+    double acc = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < p.n; s += stride) {
+        if constexpr (std::is_same<T, double>::value) {
+            double r = 0.0;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) r += Store<S>::ld(A + i * p.pstride + s);
+            acc += r;
+        } else {
+            float sum = 0.0f, cor = 0.0f;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const float x = Store<S>::ld(A + i * p.pstride + s);
+                const float t = sum + x, bb = t - sum;
+                cor += (sum - (t - bb)) + (x - bb);
+                sum = t;
+            }
+            acc += (double)sum + (double)cor;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        if (Store<S>::SHIFT && blockIdx.x == 0) v += (double)p.n * p.d.rho_ref;
+        partials[blockIdx.x * 4] = v;
+        partials[blockIdx.x * 4 + 1] = partials[blockIdx.x * 4 + 2] = partials[blockIdx.x * 4 + 3] = 0.0;
+    }
+}
+
 // ----------------------------------------------------------------- launchers
 template <class L, class S> struct Launch {
     using PsiT = typename Store<S>::PsiT;
@@ -301,7 +348,7 @@ template <class L, class S> struct Launch {
         int by = threads / bx;
         if (by > p.ny) by = p.ny;
         block = dim3(bx, by, 1);
-        grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+        grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nzl);
     }
     // Two cells per thread with packed FP32 arithmetic where it applies (FP32 arithmetic,
     // even nx, fewer than 2^31 cells); one cell per thread otherwise.
@@ -316,7 +363,7 @@ template <class L, class S> struct Launch {
         int by = threads / bx;
         if (by > p.ny) by = p.ny;
         block = dim3(bx, by, 1);
-        grid = dim3((npx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+        grid = dim3((npx + bx - 1) / bx, (p.ny + by - 1) / by, p.nzl);
     }
     template <bool ODD> static void psi_t(const KParams &p, const void *A, void *psi, cudaStream_t st) {
         dim3 grid, block;
@@ -358,7 +405,7 @@ template <class L, class S> struct Launch {
                 // every SM) later; FP16S is bound by arithmetic and loses more to the extra
                 // instructions than it gains
                 KParams q = p;
-                if (std::is_same<S, float>::value && PLB_L2_PREFETCH) {
+                if ((std::is_same<S, float>::value ? PLB_L2_PREFETCH : PLB_L2_PREFETCH_HALF) != 0) {
                     const int ahead = PLB_PF_WAVES * pair_blocks_per_sm<MRT, ODD>() * sm_count();
                     q.prefetch_ahead = ahead;
                     q.pf_step[0] = ahead % (int)grid.x;
@@ -414,6 +461,9 @@ template <class L, class S> struct Launch {
         k_reduce<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, (const PsiT *)psi, odd, what, lo[0], lo[1], lo[2],
                                                 hi[0], hi[1], hi[2], partials);
     }
+    static void mass(const KParams &p, const void *A, double *partials, int nblocks, cudaStream_t st) {
+        k_mass_flat<L, S><<<nblocks, 256, 0, st>>>(p, (const S *)A, partials);
+    }
     static void wall_fill(const KParams &p, void *psi, cudaStream_t st) {
         const long long n = ((long long)p.nx + 2) * (L::D == 3 ? p.nz + 2 : 1);
         k_wall_fill<L, S><<<blocks(n, 256), 256, 0, st>>>(p, (PsiT *)psi);
@@ -453,7 +503,8 @@ template <class L, class S> struct Launch {
         return Launchers{&init,     &psi,    {&collide_bgk, &collide_mrt}, &moments, &get_pops, &set_pops, &reduce,
                          {&batch_bgk, &batch_mrt}, &rebalance, &wall_fill,
                          {std::is_same<S, double>::value ? nullptr : &fused_bgk,
-                          std::is_same<S, double>::value ? nullptr : &fused_mrt}};
+                          std::is_same<S, double>::value ? nullptr : &fused_mrt},
+                         &mass};
     }
 };
 

@@ -41,6 +41,8 @@ struct PlainPhys {
 
 struct KParams {
     int nx, ny, nz;
+    int z0, nzl;          // the step kernels update planes z0 <= z < z0 + nzl (a slab: the planes between
+                          // its two ghost planes; else 0 and nz)
     long long n;          // cells
     long long pstride;    // elements between population planes
     int wall_y;
@@ -55,6 +57,7 @@ struct KParams {
     int prefetch_ahead;   // k_collide_pair: prefetch into L2 for the block this many launch slots later (0: off)
     int pf_step[3];       // that offset split along the grid axes (x, y, z), for carry propagation
     unsigned salt;        // step counter mixed into the rounding noise
+    unsigned cell_base;   // added to the cell index hashed for the rounding noise (a slab: its offset)
     Phys<double> d;
     Phys<float> f;
     PlainPhys pl;
@@ -108,6 +111,8 @@ struct Launchers {
     void (*wall_fill)(const KParams &, void *psi, cudaStream_t);
     // single-pass step [BGK, MRT]: reads A (natural layout), pushes into B; NULL for FP64
     void (*fused[2])(const KParams &, const void *A, void *B, cudaStream_t);
+    // total mass of the whole lattice, one partial per block (slot 0 of 4)
+    void (*mass)(const KParams &, const void *A, double *partials, int nblocks, cudaStream_t);
 };
 
 // Defined in plb_kern_fp64.cu / plb_kern_fp32.cu / plb_kern_fp16.cu; lattice 0 = D2Q9, 1 = D3Q19.

@@ -9,7 +9,16 @@
 // The psi stencil of the two cells is read as float2 vectors: 3 per row where the
 // stencil spans x0 - 1 .. x0 + 2, 1 where it spans x0 .. x0 + 1.
 #pragma once
+#include "plb_moment.cuh"
 #include "plb_step.cuh"
+
+// D3Q19 collision of the pair kernels: 0 = the per-pair BGK update with the ghost-moment
+// correction (collide_emit) for every storage; 1 = the moment-space collision
+// (collide_moments_d3q19) for FP16-shifted storage, collide_emit for FP32; 2 = the moment-space
+// collision for both.
+#ifndef PLB_MOMENT_COLLIDE
+#define PLB_MOMENT_COLLIDE 1
+#endif
 
 namespace plb {
 
@@ -81,7 +90,7 @@ __device__ __forceinline__ void geo_pair_at(const KParams &p, int x0, int y, int
 __device__ __forceinline__ bool make_geo_pair(const KParams &p, GeoPair &g) {
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return false;
-    geo_pair_at(p, x0, y, blockIdx.z, g);
+    geo_pair_at(p, x0, y, blockIdx.z + p.z0, g);
     return true;
 }
 
@@ -137,13 +146,20 @@ __device__ __forceinline__ void store_dir(const KParams &p, const Planes<S> &A, 
 }
 
 // Collision of the pair with each population stored as soon as it is final (collide_emit).
+template <class L, class S> struct UseMomentCollide {
+    static constexpr bool value =
+        std::is_same<L, D3Q19>::value && (PLB_MOMENT_COLLIDE == 2 || (PLB_MOMENT_COLLIDE == 1 && Store<S>::SHIFT));
+};
+
 template <class L, class S, int MRT, bool ODD, bool WALL, bool SR>
 __device__ __forceinline__ void collide_store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 *f,
                                                    const f2 F[3], unsigned salt) {
-    const unsigned hsh = SR ? cell_hash((unsigned)g.s0, salt) : 0u;
-    collide_emit<L, MRT, Store<S>::SHIFT, f2>(p, f, F, [&](auto ic, const f2 &v) {
-        store_dir<L, S, ODD, WALL, SR, decltype(ic)::value>(p, A, g, v, hsh);
-    });
+    const unsigned hsh = SR ? cell_hash((unsigned)g.s0 + p.cell_base, salt) : 0u;
+    auto emit = [&](auto ic, const f2 &v) { store_dir<L, S, ODD, WALL, SR, decltype(ic)::value>(p, A, g, v, hsh); };
+    if constexpr (UseMomentCollide<L, S>::value)
+        collide_moments_d3q19<MRT, Store<S>::SHIFT, f2>(p, f, F, emit);
+    else
+        collide_emit<L, MRT, Store<S>::SHIFT, f2>(p, f, F, emit);
 }
 
 // Force densities of the two cells from their psi stencil; at(cx, cy, cz) returns psi of both
@@ -322,7 +338,7 @@ __device__ __forceinline__ void prefetch_ahead_pair(const KParams &p, const Plan
     if (bz >= (int)gridDim.z) return;
     const int x0 = 2 * (bx * blockDim.x + threadIdx.x), y = by * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
-    const int s0 = x0 + p.nx * (y + p.ny * bz);
+    const int s0 = x0 + p.nx * (y + p.ny * (bz + p.z0));
     Unroll<0, L::Q>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(A.p[i] + s0));

@@ -43,7 +43,7 @@ template <class I> __device__ __forceinline__ void geo_at(const KParams &p, int 
 template <class I> __device__ __forceinline__ bool make_geo(const KParams &p, Geo<I> &g) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= p.nx || y >= p.ny) return false;
-    geo_at<I>(p, x, y, blockIdx.z, g);
+    geo_at<I>(p, x, y, blockIdx.z + p.z0, g);
     return true;
 }
 
@@ -74,7 +74,7 @@ template <class L, class S, bool ODD, bool WALL, bool SR = false, class I>
 __device__ __forceinline__ void store_fast(const KParams &p, const Planes<S> &A, const Geo<I> &g,
                                            const typename Store<S>::T *f, unsigned salt = 0) {
     unsigned hsh = 0;
-    if constexpr (SR) hsh = cell_hash((unsigned)g.s, salt);
+    if constexpr (SR) hsh = cell_hash((unsigned)g.s + p.cell_base, salt);
     auto st = [&](S *a, typename Store<S>::T v, int i) {
         if constexpr (SR) Store<S>::st_sr(a, v, dir_bits(hsh, i));
         else Store<S>::st(a, v);
