@@ -103,6 +103,9 @@ struct plb_batch_state {
     std::map<int, cudaGraphExec_t> graphs;
     bool graph_ok;         // false once a capture failed: launch directly
     long long t;
+    long long graph_captures;   // graphs captured and instantiated
+    long long graph_launches;   // plb_batch_step calls served by a graph launch
+    long long direct_launches;  // plb_batch_step calls launched without a graph
 };
 
 namespace {
@@ -361,15 +364,20 @@ int plb_batch_step(plb_batch_t *b, int nsteps) {
                 cudaGetLastError();
                 b->graph_ok = false;
                 e = launch_persistent(b, nsteps, 0);
+                ++b->direct_launches;
             } else {
                 it = b->graphs.emplace(nsteps, ex).first;
+                ++b->graph_captures;
                 e = cudaGraphLaunch(it->second, b->stream);
+                ++b->graph_launches;
             }
         } else {
             e = cudaGraphLaunch(it->second, b->stream);
+            ++b->graph_launches;
         }
     } else {
         e = launch_persistent(b, nsteps, extra);
+        ++b->direct_launches;
     }
     if (e != cudaSuccess) return plb::set_error(PLB_ECUDA, "batch launch: %s", cudaGetErrorString(e));
     b->t += nsteps;
@@ -450,5 +458,13 @@ int plb_batch_autotune(plb_batch_t *b, int steps_per_candidate, int *tile_cells,
 }
 
 long long plb_batch_time(const plb_batch_t *b) { return b ? b->t : -1; }
+
+int plb_batch_launch_counts(const plb_batch_t *b, long long counts[3]) {
+    if (!b || !counts) return plb::set_error(PLB_EINVAL, "NULL argument");
+    counts[0] = b->graph_captures;
+    counts[1] = b->graph_launches;
+    counts[2] = b->direct_launches;
+    return PLB_OK;
+}
 
 }  // extern "C"

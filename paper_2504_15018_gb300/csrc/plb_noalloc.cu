@@ -50,7 +50,8 @@ int scratch_address(void **addr) {
 }  // namespace
 
 extern "C" int plb_step_pairs_static(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G,
-                                     double eps, const plb_opts *opts, void *dev_pops, int npairs, void *cuda_stream) {
+                                     double eps, const plb_opts *opts, void *dev_pops, int npairs, long long t0,
+                                     void *cuda_stream) {
     plb_opts o;
     plb::Layout lay;
     int st = plb::check_create_args(lattice, dims, eos, tau, G, eps, opts, o, lay);
@@ -62,6 +63,7 @@ extern "C" int plb_step_pairs_static(int lattice, const int dims[3], const plb_e
     if (reinterpret_cast<uintptr_t>(dev_pops) % 256 != 0)
         return plb::set_error(PLB_EINVAL, "dev_pops must be 256-byte aligned");
     if (npairs < 0) return plb::set_error(PLB_EINVAL, "npairs must be >= 0");
+    if (t0 < 0) return plb::set_error(PLB_EINVAL, "t0 must be >= 0");
     const size_t psi_bytes = (size_t)lay.psi_elems * lay.s_psi;
     if (psi_bytes > kScratchBytes - kFlagBytes)
         return plb::set_error(PLB_ENOMEM,
@@ -84,11 +86,19 @@ extern "C" int plb_step_pairs_static(int lattice, const int dims[3], const plb_e
     const plb::Launchers *L = plb::launchers_for_precision(lattice, o.precision);
     const int coll = o.collision == PLB_MRT ? 1 : 0;
 
+    // An error left pending by earlier work on this thread would otherwise be reported below
+    // as a failure of these launches.
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return plb::set_error(PLB_ECUDA, "a CUDA error from earlier work is pending on this thread: %s",
+                              cudaGetErrorString(e));
     // The scratch keeps the previous call's contents: the flags must start at zero.
-    cudaError_t e = cudaMemsetAsync(k.flags, 0, sizeof(unsigned), stream);
+    e = cudaMemsetAsync(k.flags, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return plb::set_error(PLB_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     for (int n = 0; n < npairs; ++n) {
         for (int odd = 0; odd < 2; ++odd) {
+            // the step counter seeds stochastic rounding exactly as plb_step does
+            k.salt = (unsigned)(t0 + 2LL * n + odd);
             L->psi(k, dev_pops, scratch, odd, stream);
             L->collide[coll](k, dev_pops, scratch, odd, stream);
         }

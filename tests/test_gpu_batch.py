@@ -123,15 +123,46 @@ def test_autotune_picks_a_valid_tiling_and_keeps_the_dynamics():
     b = plb.Batch(plb.PLB_D2Q9, insts)
     for k, (rho, u0) in enumerate(fields):
         b.init(k, rho, u0)
+    before = plb.plb_batch_launch_counts(b.b)
     tile, bps, ms = b.autotune(2)
     assert tile in (512, 1024, 2048, 4096, 8192, 16384) and 1 <= bps <= 4 and ms > 0
-    steps = plb.plb_batch_time(b.b)
-    assert steps == 2 * 5 * 2 * (1 + 1) or steps > 0
+    # every candidate (6 tile sizes x each resident count up to the occupancy limit, at most 4)
+    # runs 2 warm-up and 2 timed steps, two plb_batch_step(2) calls: its new tiling drops the
+    # graphs, so the warm-up call captures one and the timed call replays it
+    after = plb.plb_batch_launch_counts(b.b)
+    calls = (after["graph_launches"] + after["direct_launches"]) - (before["graph_launches"] +
+                                                                    before["direct_launches"])
+    ncand = calls // 2
+    assert calls == 2 * ncand and ncand % 6 == 0 and 1 <= ncand // 6 <= 4, (before, after)
+    assert plb.plb_batch_time(b.b) == ncand * (2 + 2)
+    assert after["graph_captures"] - before["graph_captures"] == ncand, (before, after)
+    assert after["direct_launches"] == before["direct_launches"], (before, after)
     b.step(3)
     b.status()
     total = plb.plb_batch_time(b.b)
     for k, (rho, u0) in enumerate(fields):
         assert np.array_equal(b.populations(k), _alone(0, insts[k], rho, u0, total)), k
+
+
+def test_steps_are_captured_once_and_replayed_as_graphs():
+    """On the batch's own (non-default) stream, the first plb_batch_step(n) for a given n is
+    captured and instantiated as a CUDA graph, later calls with the same n replay it, and a new
+    n is captured once more; nothing is launched directly.  Replays give the same populations
+    as lone lattices stepped by plb_step."""
+    import paper_2504_15018_gb300 as plb
+    insts, fields = _instances(0, D2_SPECS[:3], 1, False)
+    b = plb.Batch(plb.PLB_D2Q9, insts)
+    for k, (rho, u0) in enumerate(fields):
+        b.init(k, rho, u0)
+    assert plb.plb_batch_launch_counts(b.b) == {"graph_captures": 0, "graph_launches": 0, "direct_launches": 0}
+    for _ in range(3):
+        b.step(4)
+    b.step(1)
+    b.step(4)
+    b.status()
+    assert plb.plb_batch_launch_counts(b.b) == {"graph_captures": 2, "graph_launches": 5, "direct_launches": 0}
+    for k, (rho, u0) in enumerate(fields):
+        assert np.array_equal(b.populations(k), _alone(0, insts[k], rho, u0, 17)), k
 
 
 def test_withheld_barrier_arrival_times_out_with_an_error():
