@@ -276,18 +276,22 @@ def run_gpu(args):
         barrier()
         t0 = time.perf_counter()
         plb.plb_init(lat.h, rho_pin)
+        t1 = time.perf_counter()
         lat.step(args.steps)
         mass = lat.reduce(plb.PLB_MASS)[0]
+        t2 = time.perf_counter()
         plb.plb_moments(lat.h, out_rho, out_u, out_p)
         barrier()
         te = time.perf_counter() - t0
+        parts = {"init_ms": round((t1 - t0) * 1e3, 3), "steps_and_mass_ms": round((t2 - t1) * 1e3, 3),
+                 "moments_ms": round((t0 + te - t2) * 1e3, 3)}
         te = max_over_ranks(te, world, "cuda")
         h2d = rho_pin.numel() * 8
         d2h = (out_rho.numel() + out_u.numel() + out_p.numel()) * 8 + 8
         e2e = {"value": round(job_glups(ncell, args.steps, te, world), 4), "unit": "GLUPS",
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                "what": "plb_init from pinned host rho0 + K steps + plb_reduce(mass) + plb_moments to pinned host",
-               "mass": mass}
+               "mass": mass, "parts": parts}
     del lat
     torch.cuda.empty_cache()
 

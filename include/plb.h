@@ -288,6 +288,69 @@ int plb_batch_withhold_arrivals(plb_batch_t *b, unsigned count);
 /* Steps taken by the batch; -1 for a NULL batch. */
 long long plb_batch_time(const plb_batch_t *b);
 
+/* How plb_batch_step calls were launched since the batch was created: counts[0] = CUDA graphs
+ * captured and instantiated (one per distinct nsteps on a non-default stream, captured again
+ * after plb_batch_configure), counts[1] = calls served by a graph launch, counts[2] = calls
+ * launched directly (the default stream, a withheld-arrival test launch, or a stream whose
+ * capture failed).  PLB_EINVAL for NULL arguments. */
+int plb_batch_launch_counts(const plb_batch_t *b, long long counts[3]);
+
+/* ---------------------------------------------------------------- slab decomposition
+ * One D3Q19 lattice of nx x ny x NZ cells, periodic in z, split along z into slabs (one per
+ * GPU, or several on one GPU).  The force of Eq. interactionForce reaches the nearest
+ * neighbours only (Sec. IV), so each step exchanges a one-plane psi halo after the psi pass and
+ * five population planes per face after the collide pass.  A slab owning the global planes
+ * z_first .. z_first + m - 1 is an ordinary handle (plb_create) of dims (nx, ny, m + 2) whose
+ * local planes 0 and m + 1 are ghost planes (copies of global planes z_first - 1 and z_first + m,
+ * wrapped periodically); plb_init is given the m + 2 planes.  After plb_slab_bind, plb_step
+ * refuses the handle: a step is
+ *     plb_slab_pass(h, 0) on every slab;  the pass-0 exchange across every face;
+ *     plb_slab_pass(h, 1) on every slab;  the pass-1 exchange across every face,
+ * and the owned planes then equal the same planes of the whole lattice stepped by plb_step, bit
+ * for bit (same kernels; stochastic rounding hashes the whole lattice's cell index).  Readouts
+ * of a slab handle cover its m + 2 planes; the ghost planes' moments are not meaningful.
+ * D3Q19 only, in place (AA) streaming only; walls in y allowed. */
+
+/* One transfer of the exchange plan: bytes from send_off on this slab to recv_off on the
+ * neighbour across `face` (0: toward lower z, 1: toward higher z), offsets in bytes from the
+ * start of the population store (region 0) or of the padded psi field (region 1), as returned
+ * by plb_slab_regions.  Entry k of face f on one slab pairs with entry k of face 1 - f on the
+ * neighbour: that entry's send range arrives in this entry's receive range and vice versa. */
+typedef struct {
+    long long send_off, recv_off, bytes;
+    int face, region;
+} plb_xfer;
+
+/* The exchange plan after pass `pass` (0: psi pass, 1: collide pass) of a step of AA parity
+ * `odd` (the parity the step had when its passes ran), for a slab of local dims (nx, ny, m + 2),
+ * storage `precision`, walls in y or not.  Host-only (no device work): pass 0 lists two psi
+ * planes, pass 1 ten population planes (after an even step the slots that the neighbour's odd
+ * step reads; after an odd step the slots this slab's boundary cells streamed into its ghost
+ * planes, less the wall row of the slots whose upstream cell is beyond a wall).  out[max]:
+ * caller's array; *count receives the number of entries.  PLB_EUNSUPPORTED for D2Q9,
+ * PLB_EINVAL for bad arguments or max too small. */
+int plb_slab_plan(int lattice, const int dims[3], int precision, int wall_y, int pass, int odd, plb_xfer *out,
+                  int max, int *count);
+
+/* Makes h (D3Q19, in-place streaming, at an even step) a slab owning global planes from
+ * z_first on: its first and last local planes become ghost planes. */
+int plb_slab_bind(plb_t *h, int z_first);
+
+/* Pass 0 (psi pass) or 1 (collide pass; advances the step) over the owned planes, in the order
+ * 0, 1, 0, 1, ...  Asynchronous on the handle's stream. */
+int plb_slab_pass(plb_t *h, int pass);
+
+/* Device base addresses of the population store and of the padded psi field (the offsets of
+ * plb_slab_plan are relative to them). */
+int plb_slab_regions(plb_t *h, void **pops, void **psi);
+
+/* Carries out the exchange after pass `pass` across the face between two slabs, `lower` owning
+ * the planes just below `upper`'s (periodic: the last slab is below the first), with
+ * cudaMemcpyAsync on lower's stream (device memory of any GPUs the runtime can copy between).
+ * The caller orders the two handles' streams around it.  PLB_EINVAL unless both handles are
+ * slabs of the same cross-section, precision and walls, just after that pass of the same step. */
+int plb_slab_exchange(plb_t *lower, plb_t *upper, int pass);
+
 /* Allocation-free stepping, for callers that cannot allocate device memory: a plugin
  * that lives inside another framework's memory arena and only receives the buffers it
  * works on, or a real-time loop in which cudaMalloc (which may synchronise the device) is
@@ -298,8 +361,11 @@ long long plb_batch_time(const plb_batch_t *b);
  * plb_step.  dev_pops: caller-owned device array of Q * N stored populations, direction-major
  * f[i * N + s] in the plb_velocity_set() order, element type double (PLB_FP64), float
  * (PLB_FP32) or half holding f_i - w_i rho_ref (PLB_FP16S); 256-byte aligned; updated in place
- * and, after an even number of steps, again in this natural layout.  The other arguments are
- * those of plb_create.
+ * and, after an even number of steps, again in this natural layout.  t0 >= 0: the time step
+ * the populations are at (what plb_time would report for a lattice in this state); step
+ * t0 + m draws its stochastic-rounding noise (PLB_FP16S with fp16_rounding = 1) from the
+ * counter t0 + m, as plb_step does, so the result equals plb_step's bit for bit.  The other
+ * arguments are those of plb_create.
  *
  * Scratch: the padded psi field and the error flags live in one file-scope device array of
  * 8 MiB that every GPU loading this library holds until the process exits.  The padded psi
@@ -307,15 +373,20 @@ long long plb_batch_time(const plb_batch_t *b);
  * [x (nz + 2)], 4 bytes per value, 8 for PLB_FP64; e.g. a 120^3 D3Q19 lattice in FP32); larger
  * lattices are rejected with PLB_ENOMEM and a message.  The function calls no cudaMalloc,
  * cudaFree or other allocating routine.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  Every call shares the array and leaves its contents behind; the flags are
- * cleared at the start of each call.  Calls whose work overlaps on the GPU (different
- * streams, or without an ordering between them) race on the array.
+ * device address (cudaGetSymbolAddress) for that device and keeps it for the life of the
+ * process; make that first call before any stream capture.  After cudaDeviceReset (or anything
+ * else that tears down the device's primary context) the kept address is stale: do not call
+ * this entry point again in that process.  Every call shares the array and leaves its contents
+ * behind; the flags are cleared at the start of each call.  Calls whose work overlaps on the
+ * GPU (different streams, or without an ordering between them) race on the array.
  *
- * Returns after the steps have finished (synchronises the stream), with PLB_EPSI_DOMAIN or
- * PLB_ENONFINITE if a kernel met such a cell, PLB_EINVAL / PLB_ENOMEM on bad arguments. */
+ * Returns after the steps have finished (the call waits for its stream while it reads the
+ * flags back), with PLB_EPSI_DOMAIN or PLB_ENONFINITE if a kernel met such a cell, PLB_EINVAL /
+ * PLB_ENOMEM on bad arguments, and PLB_ECUDA without launching anything if a CUDA error from
+ * earlier work is still pending on the calling thread. */
 int plb_step_pairs_static(int lattice, const int dims[3], const plb_eos_params *eos, double tau, double G,
-                          double eps, const plb_opts *opts, void *dev_pops, int npairs, void *cuda_stream);
+                          double eps, const plb_opts *opts, void *dev_pops, int npairs, long long t0,
+                          void *cuda_stream);
 
 /* Message of the last failure on this thread ("" if none). */
 const char *plb_last_error(void);

@@ -65,6 +65,11 @@ class plb_instance(ctypes.Structure):
                 ("G", ctypes.c_double), ("eps", ctypes.c_double), ("opts", plb_opts)]
 
 
+class plb_xfer(ctypes.Structure):
+    _fields_ = [("send_off", ctypes.c_longlong), ("recv_off", ctypes.c_longlong), ("bytes", ctypes.c_longlong),
+                ("face", ctypes.c_int), ("region", ctypes.c_int)]
+
+
 _DP = ctypes.POINTER(ctypes.c_double)
 _IP = ctypes.POINTER(ctypes.c_int)
 _VP = ctypes.c_void_p
@@ -95,7 +100,7 @@ _SIGNATURES = {
     "plb_si_convert": (ctypes.c_int, [_DP, _DP, ctypes.c_double, _DP]),
     "plb_step_pairs_static": (ctypes.c_int, [ctypes.c_int, _IP, ctypes.POINTER(plb_eos_params), ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.POINTER(plb_opts), _VP,
-                                             ctypes.c_int, _VP]),
+                                             ctypes.c_int, ctypes.c_longlong, _VP]),
     "plb_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(plb_instance)]),
     "plb_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(plb_instance), _VP, ctypes.c_size_t,
                                         _VP, ctypes.POINTER(_VP)]),
@@ -110,6 +115,13 @@ _SIGNATURES = {
     "plb_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _IP, _IP, _DP]),
     "plb_batch_withhold_arrivals": (ctypes.c_int, [_VP, ctypes.c_uint]),
     "plb_batch_time": (ctypes.c_longlong, [_VP]),
+    "plb_batch_launch_counts": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    "plb_slab_plan": (ctypes.c_int, [ctypes.c_int, _IP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(plb_xfer), ctypes.c_int, _IP]),
+    "plb_slab_bind": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "plb_slab_pass": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "plb_slab_regions": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "plb_slab_exchange": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "plb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -266,11 +278,12 @@ def plb_si_convert(si, lat, xi: float) -> dict:
 
 
 def plb_step_pairs_static(lattice: int, dims, eos: plb_eos_params, tau: float, G: float, eps: float,
-                          opts: plb_opts | None, dev_pops: int, npairs: int, cuda_stream: int):
-    """Allocation-free stepping of a caller-owned device population array (2 * npairs steps)."""
+                          opts: plb_opts | None, dev_pops: int, npairs: int, t0: int, cuda_stream: int):
+    """Allocation-free stepping of a caller-owned device population array (2 * npairs steps from
+    time step t0)."""
     _check(lib().plb_step_pairs_static(lattice, _iptr(dims), ctypes.byref(eos), tau, G, eps,
                                        ctypes.byref(opts) if opts is not None else None, _VP(dev_pops),
-                                       int(npairs), _VP(cuda_stream)))
+                                       int(npairs), int(t0), _VP(cuda_stream)))
 
 
 def plb_batch_workspace_bytes(lattice: int, instances) -> int:
@@ -334,6 +347,40 @@ def plb_batch_withhold_arrivals(b, count: int):
 
 def plb_batch_time(b) -> int:
     return lib().plb_batch_time(b)
+
+
+def plb_batch_launch_counts(b) -> dict:
+    c = (ctypes.c_longlong * 3)()
+    _check(lib().plb_batch_launch_counts(b, c))
+    return {"graph_captures": c[0], "graph_launches": c[1], "direct_launches": c[2]}
+
+
+def plb_slab_plan(lattice: int, dims, precision: int, wall_y: int, pass_: int, odd: int) -> list:
+    """The exchange plan of a slab (host-only): a list of dicts with send_off, recv_off, bytes,
+    face and region."""
+    out = (plb_xfer * 16)()
+    n = ctypes.c_int(0)
+    _check(lib().plb_slab_plan(lattice, _iptr(dims), precision, int(wall_y), int(pass_), int(odd), out, 16,
+                               ctypes.byref(n)))
+    return [{k: getattr(out[i], k) for k, _ in plb_xfer._fields_} for i in range(n.value)]
+
+
+def plb_slab_bind(h, z_first: int):
+    _check(lib().plb_slab_bind(h, int(z_first)))
+
+
+def plb_slab_pass(h, pass_: int):
+    _check(lib().plb_slab_pass(h, int(pass_)))
+
+
+def plb_slab_regions(h):
+    a, b = _VP(), _VP()
+    _check(lib().plb_slab_regions(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def plb_slab_exchange(lower, upper, pass_: int):
+    _check(lib().plb_slab_exchange(lower, upper, int(pass_)))
 
 
 # ------------------------------------------------------------------- helpers

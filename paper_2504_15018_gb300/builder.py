@@ -32,6 +32,7 @@ UNITS = [
     ("plb_params.cpp", []),
     ("plb_noalloc.cu", []),
     ("plb_batch.cu", []),
+    ("plb_slab.cu", []),
 ]
 
 

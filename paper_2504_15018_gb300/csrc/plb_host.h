@@ -69,6 +69,8 @@ struct plb_state {
     long long t;
     int odd;
     int view;                  // 1: an instance of a batch (stepped only by plb_batch_step)
+    int slab;                  // 1: a z-slab whose first and last planes are ghost planes (plb_slab_*)
+    int slab_stage;            // slab: 0 = the next pass is the psi pass, 1 = the collide pass
 };
 
 namespace plb {

@@ -116,6 +116,19 @@ long long stage_cells(const plb::Layout &L, int need) {
     return c < L.n ? c : L.n;
 }
 
+// Device address of a caller's buffer that kernels can access directly (device or managed
+// memory, or pinned / registered host memory), else NULL (pageable host memory).
+template <class T> T *device_view(T *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost)
+        return static_cast<T *>(a.devicePointer);
+    return nullptr;
+}
+
 int check_launch() {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PLB_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -234,6 +247,8 @@ int fill_kparams(const int dims[3], const plb_eos_params &eos, double tau, doubl
     k.nx = dims[0];
     k.ny = dims[1];
     k.nz = dims[2];
+    k.z0 = 0;
+    k.nzl = dims[2];
     k.n = lay.n;
     k.pstride = lay.pstride;
     k.wall_y = o.wall_y ? 1 : 0;
@@ -423,9 +438,16 @@ int plb::init_state(plb_state *h, const double *rho0, const double *u0) {
     // costs tens of milliseconds): flags cleared, first-invalid-index slots set to all ones
     PLB_CUDA(cudaMemsetAsync(h->kp.flags, 0, 64, h->stream));
     PLB_CUDA(cudaMemsetAsync(h->kp.flags + plb::FLAG_SLOT_RHO, 0xff, 16, h->stream));
+    const double *drho0 = device_view(rho0), *du0 = u0 ? device_view(u0) : nullptr;
+    if (drho0 && (!u0 || du0)) {
+        // inputs the device can read: one launch over all cells
+        h->L->init(h->kp, pops_ptr(h), drho0, du0, 0, n, h->stream);
+        int st = check_launch();
+        if (st) return st;
+    }
     double *stg = staging_ptr(h);
     const long long chunk = stage_cells(h->lay, 1 + (u0 ? h->lay.D : 0));
-    for (long long c0 = 0; c0 < n; c0 += chunk) {
+    for (long long c0 = (drho0 && (!u0 || du0)) ? n : 0; c0 < n; c0 += chunk) {
         const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
         PLB_CUDA(cudaMemcpyAsync(stg, rho0 + c0, cn * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         if (u0)
@@ -462,6 +484,7 @@ extern "C" {
 int plb_step(plb_t *h, int n) {
     if (!h || n < 0) return fail(PLB_EINVAL, "bad argument");
     if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
+    if (h->slab) return fail(PLB_EINVAL, "this lattice is a slab: step it with plb_slab_pass and plb_slab_exchange");
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
     if (h->pops2) {
         // single pass: read the current copy, push into the other, swap
@@ -486,6 +509,7 @@ int plb_step(plb_t *h, int n) {
 int plb_step_timed(plb_t *h, int n, double ms[2]) {
     if (!h || n < 0 || !ms) return fail(PLB_EINVAL, "bad argument");
     if (h->view) return fail(PLB_EINVAL, "this lattice belongs to a batch: use plb_batch_step");
+    if (h->slab) return fail(PLB_EINVAL, "this lattice is a slab: step it with plb_slab_pass and plb_slab_exchange");
     ms[0] = ms[1] = 0.0;
     if (n == 0) return PLB_OK;
     const int coll = h->opts.collision == PLB_MRT ? 1 : 0;
@@ -540,6 +564,17 @@ int plb_moments(plb_t *h, double *rho, double *u, double *p) {
     h->L->psi(h->kp, pops_ptr(h), psi_ptr(h), h->odd, h->stream);
     const int D = h->lay.D;
     const long long n = h->lay.n, chunk = stage_cells(h->lay, D + 2);
+    // Outputs the device can write (device memory, or host memory the runtime has pinned or
+    // registered): one launch writes them directly; otherwise chunks go through the staging area.
+    double *drho = rho ? device_view(rho) : nullptr, *du = u ? device_view(u) : nullptr;
+    double *dp = p ? device_view(p) : nullptr;
+    if ((!rho || drho) && (!u || du) && (!p || dp)) {
+        h->L->moments(h->kp, pops_ptr(h), psi_ptr(h), h->odd, drho, du, dp, 0, n, h->stream);
+        int st = check_launch();
+        if (st) return st;
+        PLB_CUDA(cudaStreamSynchronize(h->stream));
+        return plb_status(h);
+    }
     double *stg = staging_ptr(h);
     for (long long c0 = 0; c0 < n; c0 += chunk) {
         const long long cn = (n - c0) < chunk ? (n - c0) : chunk;
@@ -576,7 +611,12 @@ int plb_reduce(plb_t *h, int what, const int lo[3], const int hi[3], double *out
     const int nblocks = (int)(nb < h->lay.max_blocks ? nb : h->lay.max_blocks);
     double *partials = h->partials;
     double *dout = h->out;
-    h->L->reduce(h->kp, pops_ptr(h), psi_ptr(h), h->odd, what, blo, bhi, partials, nblocks, h->stream);
+    const bool whole = blo[0] == 0 && blo[1] == 0 && blo[2] == 0 && bhi[0] == h->dims[0] &&
+                       bhi[1] == h->dims[1] && bhi[2] == h->dims[2];
+    if (what == PLB_MASS && whole)
+        h->L->mass(h->kp, pops_ptr(h), partials, nblocks, h->stream);
+    else
+        h->L->reduce(h->kp, pops_ptr(h), psi_ptr(h), h->odd, what, blo, bhi, partials, nblocks, h->stream);
     int st = check_launch();
     if (st) return st;
     reduce_final_launch(partials, nblocks, what == PLB_UMAX, dout, h->stream);
