@@ -9,6 +9,7 @@
 #include "plb_batch.cuh"
 #include "plb_fused.cuh"
 #include "plb_pair.cuh"
+#include "plb_staged.cuh"
 #include "plb_step.cuh"
 
 // L2 prefetch one wave ahead in the FP32 fused pass (1) or not (0).
@@ -22,6 +23,18 @@
 // L2 prefetch distance of the fused pass in waves of resident blocks.
 #ifndef PLB_PF_WAVES
 #define PLB_PF_WAVES 1
+#endif
+// D3Q19 fused pass with the next plane staged in shared memory (plb_staged.cuh): FP16S storage
+// (PLB_STAGED_HALF) and FP32 storage (PLB_STAGED_FLOAT).
+#ifndef PLB_STAGED_HALF
+#define PLB_STAGED_HALF 1
+#endif
+#ifndef PLB_STAGED_FLOAT
+#define PLB_STAGED_FLOAT 0
+#endif
+// psi pass of FP16S storage over four cells per thread where nx is a multiple of 4.
+#ifndef PLB_PSI_QUAD
+#define PLB_PSI_QUAD 1
 #endif
 // Two cells per thread for FP16 storage (1) or one (0).
 #ifndef PLB_HALF_PAIR
@@ -367,6 +380,17 @@ template <class L, class S> struct Launch {
     }
     template <bool ODD> static void psi_t(const KParams &p, const void *A, void *psi, cudaStream_t st) {
         dim3 grid, block;
+        if constexpr (std::is_same<S, __half>::value) {
+            if (PLB_PSI_QUAD && p.nx % 4 == 0 && p.n < (1LL << 31)) {
+                const int nq = p.nx / 4;
+                const int bx = nq >= 64 ? 64 : (nq + 31) / 32 * 32;
+                int by = 256 / bx;
+                if (by > p.ny) by = p.ny;
+                k_psi_quad<L, ODD><<<dim3((nq + bx - 1) / bx, (p.ny + by - 1) / by, p.nzl), dim3(bx, by), 0, st>>>(
+                    p, planes(p, A), (float *)psi);
+                return;
+            }
+        }
         if constexpr (!std::is_same<S, double>::value) {
             if (use_pair(p)) {
                 dims_pair(p, grid, block);
@@ -399,6 +423,21 @@ template <class L, class S> struct Launch {
     template <int MRT, bool ODD> static void collide_t(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         dim3 grid, block;
         if constexpr (!std::is_same<S, double>::value) {
+            if (use_pair(p) && std::is_same<L, D3Q19>::value &&
+                (std::is_same<S, __half>::value ? PLB_STAGED_HALF : PLB_STAGED_FLOAT) != 0) {
+                constexpr int per = 2 * StagedShape<L>::THREADS;
+                const dim3 sgrid((p.nx + per - 1) / per, p.ny, (p.nzl + PLB_STAGED_ZC - 1) / PLB_STAGED_ZC);
+                const dim3 sblock(StagedShape<L>::THREADS);
+                if constexpr (Store<S>::SHIFT) {
+                    if (p.stochastic) {
+                        k_collide_staged<L, S, MRT, ODD, true><<<sgrid, sblock, 0, st>>>(p, planes(p, A),
+                                                                                         (const float *)psi);
+                        return;
+                    }
+                }
+                k_collide_staged<L, S, MRT, ODD, false><<<sgrid, sblock, 0, st>>>(p, planes(p, A), (const float *)psi);
+                return;
+            }
             if (use_pair(p)) {
                 dims_pair(p, grid, block, PLB_PAIR_THREADS);
                 // FP32 storage: prefetch into L2 for the block one wave (the resident blocks of

@@ -164,8 +164,56 @@ __device__ __forceinline__ void collide_store_pair(const KParams &p, const Plane
 
 // Force densities of the two cells from their psi stencil; at(cx, cy, cz) returns psi of both
 // cells at offset (cx, cy, cz) (the global or the shared-memory psi field).
+// D3Q19 force stencil summed by velocity class (1) or direction by direction (0).
+#ifndef PLB_GROUPED_FORCE
+#define PLB_GROUPED_FORCE 1
+#endif
+
+// D3Q19: the moments summed by velocity class.  With dif_r / sum_r = psi(x + c_r) -+ psi(x - c_r)
+// for the pairs r (axes x, y, z; (1, +-1, 0); (1, 0, +-1); (0, 1, +-1)), 3 w = 1/6 (axes) and
+// 1/12 (edges), 9 w = 1/2 and 1/4, and 9 w_0 (0 - 1/3) = -1 at the rest velocity:
+//   M1_x = dif_x / 6 + (dif_xy+ + dif_xy- + dif_xz+ + dif_xz-) / 12        (and y, z)
+//   M2_xx = K + sum_x / 2 - S_yz / 4,   K = (S_edges - S_axes) / 6 - psi0    (and yy, zz)
+//   M2_xy = (sum_xy+ - sum_xy-) / 4                                          (and xz, yz)
+//   tr M2 = S_edges / 4 - 3 psi0
+// where S_ab = sum_ab+ + sum_ab-, S_edges = S_xy + S_xz + S_yz, S_axes = sum_x + sum_y + sum_z.
+template <class At>
+__device__ __forceinline__ void force_pair_d3q19(const KParams &p, At &&at, f2 F[3]) {
+    using L = D3Q19;
+    const f2 psi0 = at(0, 0, 0);
+    f2 dif[9], sum[9];
+    Unroll<0, 9>::run([&](auto kc) {
+        constexpr int i = 2 * decltype(kc)::value + 1;
+        const f2 pa = at(L::cx(i), L::cy(i), L::cz(i)), pb = at(-L::cx(i), -L::cy(i), -L::cz(i));
+        dif[decltype(kc)::value] = pa - pb;
+        sum[decltype(kc)::value] = pa + pb;
+    });
+    const f2 m1[3] = {mad(f2(1.0f / 6.0f), dif[0], f2(1.0f / 12.0f) * ((dif[3] + dif[4]) + (dif[5] + dif[6]))),
+                      mad(f2(1.0f / 6.0f), dif[1], f2(1.0f / 12.0f) * ((dif[3] - dif[4]) + (dif[7] + dif[8]))),
+                      mad(f2(1.0f / 6.0f), dif[2], f2(1.0f / 12.0f) * ((dif[5] - dif[6]) + (dif[7] - dif[8])))};
+    const f2 Sxy = sum[3] + sum[4], Sxz = sum[5] + sum[6], Syz = sum[7] + sum[8];
+    const f2 Se = (Sxy + Sxz) + Syz, Sa = (sum[0] + sum[1]) + sum[2];
+    const f2 K = mad(f2(1.0f / 6.0f), Se - Sa, -psi0);
+    const f2 m2d[3] = {mad(f2(0.5f), sum[0], mad(f2(-0.25f), Syz, K)), mad(f2(0.5f), sum[1], mad(f2(-0.25f), Sxz, K)),
+                       mad(f2(0.5f), sum[2], mad(f2(-0.25f), Sxy, K))};
+    const f2 m2xy = f2(0.25f) * (sum[3] - sum[4]), m2xz = f2(0.25f) * (sum[5] - sum[6]),
+             m2yz = f2(0.25f) * (sum[7] - sum[8]);
+    const f2 tr = mad(f2(0.25f), Se, f2(-3.0f) * psi0);
+    const Phys<float> &q = p.f;
+    const f2 cA = f2(q.A_m1m2), cM = mad(f2(-q.G), psi0, f2(q.B_m1tr) * tr);
+    const f2 m21[3] = {mad(m2d[0], m1[0], mad(m2xy, m1[1], m2xz * m1[2])),
+                       mad(m2xy, m1[0], mad(m2d[1], m1[1], m2yz * m1[2])),
+                       mad(m2xz, m1[0], mad(m2yz, m1[1], m2d[2] * m1[2]))};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] = mad(cM, m1[a], mad(cA, m21[a], f2(q.fext[a])));
+}
+
 template <class L, class At>
 __device__ __forceinline__ void force_pair_from(const KParams &p, At &&at, f2 F[3]) {
+    if constexpr (std::is_same<L, D3Q19>::value && PLB_GROUPED_FORCE) {
+        force_pair_d3q19(p, at, F);
+        return;
+    }
     const f2 psi0 = at(0, 0, 0);
     const f2 two_psi0 = psi0 + psi0;
     f2 m1[3] = {f2(0), f2(0), f2(0)};
@@ -304,6 +352,78 @@ __global__ void __launch_bounds__(256) k_psi_pair(KParams p, Planes<S> A, float 
         psi_pair_body<L, S, ODD, true>(p, A, psi, g);
     else
         psi_pair_body<L, S, ODD, false>(p, A, psi, g);
+}
+
+// psi pass over four cells per thread for FP16-shifted storage (x0 = 4 t, nx a multiple of 4):
+// each direction is one aligned 8-byte load of the four cells' values, plus, for the x-shifted
+// reads of odd steps, one 2-byte load of the element beyond the word (periodic wrap included).
+template <class L, bool ODD, bool WALL>
+__device__ __forceinline__ void psi_quad_body(const KParams &p, const Planes<__half> &A, float *psi, int x0, int y,
+                                              int z) {
+    GeoPair g;                                  // geometry of the pair (x0, x0 + 1): rows and planes
+    geo_pair_at(p, x0, y, z, g);
+    f2 r01 = f2(0.0f), r23 = f2(0.0f);
+    auto h2f = [](unsigned w) {
+        __half2 h;
+        *reinterpret_cast<unsigned *>(&h) = w;
+        return f2(__half22float2(h));
+    };
+    Unroll<0, L::Q>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        constexpr int o = opp(i);
+        constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        bool from_wall = false;
+        if (ODD && WALL && cy != 0) from_wall = (y - cy < 0) || (y - cy >= p.ny);
+        const __half *base;
+        int r;
+        if (!ODD || from_wall) {
+            base = A.p[i];
+            r = g.s0;
+        } else {
+            base = A.p[o];
+            r = g.s0 + g.oy[1 - cy] + g.oz[1 - cz];
+        }
+        const uint2 w = __ldcs(reinterpret_cast<const uint2 *>(base + r));     // elements x0 .. x0 + 3
+        if (!ODD || cx == 0 || from_wall) {
+            r01 += h2f(w.x);
+            r23 += h2f(w.y);
+        } else if (cx > 0) {
+            // elements x0 - 1 .. x0 + 2
+            const int xl = x0 > 0 ? -1 : p.nx - 1;
+            const unsigned e = __ldcs(reinterpret_cast<const unsigned short *>(base + r + xl));
+            r01 += h2f(__byte_perm(e, w.x, 0x5410));
+            r23 += h2f(__byte_perm(w.x, w.y, 0x5432));
+        } else {
+            // elements x0 + 1 .. x0 + 4
+            const int xr = x0 + 4 < p.nx ? 4 : 4 - p.nx;
+            const unsigned e = __ldcs(reinterpret_cast<const unsigned short *>(base + r + xr));
+            r01 += h2f(__byte_perm(w.x, w.y, 0x5432));
+            r23 += h2f(__byte_perm(w.y, e, 0x5432));
+        }
+    });
+    r01 += f2(p.f.rho_ref);                        // sum_i w_i rho_ref = rho_ref
+    r23 += f2(p.f.rho_ref);
+    const f2 v01 = psi_pair_of(p, r01), v23 = psi_pair_of(p, r23);
+    float *dst = psi + psi_index(p, x0, y, z);
+    *reinterpret_cast<float4 *>(dst) = make_float4(v01.v.x, v01.v.y, v23.v.x, v23.v.y);
+    const bool by = y == 0 || y == p.ny - 1, bz = L::D == 3 && (z == 0 || z == p.nz - 1);
+    if (by || bz || x0 == 0) psi_ghosts<L>(p, psi, x0, y, z, v01.v.x);
+    if (by || bz) {
+        psi_ghosts<L>(p, psi, x0 + 1, y, z, v01.v.y);
+        psi_ghosts<L>(p, psi, x0 + 2, y, z, v23.v.x);
+    }
+    if (by || bz || x0 + 3 == p.nx - 1) psi_ghosts<L>(p, psi, x0 + 3, y, z, v23.v.y);
+}
+
+template <class L, bool ODD>
+__global__ void __launch_bounds__(256) k_psi_quad(KParams p, Planes<__half> A, float *__restrict__ psi) {
+    const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    const int z = blockIdx.z + p.z0;
+    if (ODD && p.wall_y && (y == 0 || y == p.ny - 1))
+        psi_quad_body<L, ODD, true>(p, A, psi, x0, y, z);
+    else
+        psi_quad_body<L, ODD, false>(p, A, psi, x0, y, z);
 }
 
 // Threads per block and register cap of the pair collide kernel: 64 threads and 112

@@ -58,6 +58,25 @@ def test_fused_matches_the_two_pass_kernels_bit_for_bit(name):
     assert fu.time == 13
 
 
+@pytest.mark.parametrize("name,steps", [("d3q19_fp32_mrt_walls_ragged", 100), ("d2q9_fp32_mrt_walls_taurho", 100),
+                                        ("d3q19_fp16s_mrt_walls", 50), ("d3q19_fp16s_sr_mrt_walls", 50)])
+def test_fused_against_the_oracle(name, steps):
+    """The single pass compared with the FP64 oracle directly: FP32 within the linear
+    accumulation bound steps * 8 * 2^-24 (relative), FP16S within sqrt(steps) * 2^-11 (2^-10 with
+    stochastic rounding) of w_i rho_l, as for the two-pass kernels."""
+    from gpu_cases import max_rel_err, run_both
+    case = dict(CASES[name], streaming=1)
+    ref, got, _, _ = run_both(case, steps)
+    if case["precision"] == 1:
+        err = max_rel_err(ref, got)
+        bound = steps * 8 * 2.0 ** -24
+    else:
+        err = float(np.max(np.abs(got - ref) / np.abs(ref).max(axis=1, keepdims=True)))
+        bound = np.sqrt(steps) * 2.0 ** (-10 if case.get("fp16_rounding") else -11)
+    print(f"{name} single pass, {steps} steps: error {err:.3e} (bound {bound:.2e})")
+    assert err <= bound
+
+
 def test_fused_readouts_state_and_balanced_start():
     import paper_2504_15018_gb300 as plb
     aa, fu = _pair("d3q19_fp32_mrt_walls_ragged", 5, physical=True)
