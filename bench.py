@@ -160,12 +160,14 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_kernels.cuh", "plb_pair.cuh", "plb_step.cuh")
+KERNEL_SOURCES = ("plb_device.cuh", "plb_f2.cuh", "plb_fused.cuh", "plb_kernels.cuh", "plb_moment.cuh", "plb_pair.cuh",
+                  "plb_plain.cuh", "plb_staged.cuh", "plb_step.cuh")
 
 
 def kernel_source_sha():
-    """Hash of the files that hold the step kernels' device code (k_psi_pair, k_collide_pair,
-    k_fused_pair and everything they inline) and their launch shapes."""
+    """Hash of the files that hold the step kernels' device code (k_psi_pair, k_psi_quad,
+    k_collide_pair, k_collide_staged, k_collide_plain, k_fused_pair and everything they inline)
+    and their launch shapes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_15018_gb300", "csrc")
     for f in KERNEL_SOURCES:
@@ -251,8 +253,15 @@ def run_gpu(args):
     fused_gbs = bpc["fused_pass"] * ncell * nprof / (ms_fused / 1e3) / 1e9
     peak, peak_kind = peak_hbm()
     wl = workload_name(dims, args.precision, args.collision)
-    kernel = ("k_fused_pair (psi of tile + halo in shared memory, force, collide, push stream)"
-              if args.streaming == "fused" else "k_collide_pair (fused force + collide + stream)")
+    if args.streaming == "fused":
+        kernel = "k_fused_pair (psi of tile + halo in shared memory, force, collide, push stream)"
+    elif args.precision in ("fp16s", "fp16s_sr"):
+        kernel = ("k_collide_staged (fused force + collide + stream, next plane staged in shared memory, "
+                  "moment-space collision)")
+    elif args.precision == "fp64":
+        kernel = "k_collide_plain (fused force + collide + stream, FP64 in the equations' order)"
+    else:
+        kernel = "k_collide_pair (fused force + collide + stream)"
     traffic = recorded_traffic(wl, kernel.split()[0])
     roofline = {"bound": "hbm", "kernel": kernel,
                 "achieved": round(fused_gbs, 1), "peak": peak, "unit": "GB/s",

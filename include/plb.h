@@ -108,7 +108,8 @@ typedef struct plb_opts {
                                 PLB_STREAM_FUSED: one kernel per step that forms psi of each tile and
                                 its halo in shared memory, collides and pushes into a second copy of
                                 the populations (twice the population memory, about 30 % fewer DRAM
-                                bytes per step); PLB_FP32 / PLB_FP16S with even nx only, not in
+                                bytes per step); PLB_FP32 / PLB_FP16S with even nx and population
+                                planes below 4 GiB (fewer than 2^30 / 2^31 cells) only, not in
                                 batches [PLB_STREAM_AA].  Both give the same populations. */
     double wall_rho;         /* wall_y = 1 only: > 0 makes the walls wetting walls, whose nodes carry
                                 the pseudo-potential psi(wall_rho) of a prescribed wall density

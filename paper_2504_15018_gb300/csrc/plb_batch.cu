@@ -272,7 +272,10 @@ int plb_batch_create(int lattice, int n, const plb_instance *inst, void *dev_wor
             bi.pl[i] = i < lay.Q ? static_cast<void *>(h->pops + (size_t)i * lay.pstride * lay.s_pop) : nullptr;
         bi.psi = h->psi;
         bi.odd = 0;
-        bi.pair = (b->precision != PLB_FP64 && inst[k].dims[0] % 2 == 0) ? 1 : 0;
+        // two cells per thread: FP32 arithmetic, even nx, population planes below 4 GiB
+        const long long ncell = (long long)inst[k].dims[0] * inst[k].dims[1] * inst[k].dims[2];
+        bi.pair = (b->precision != PLB_FP64 && inst[k].dims[0] % 2 == 0 &&
+                   ncell * (b->precision == PLB_FP32 ? 4 : 2) < (1LL << 32)) ? 1 : 0;
         bi.upr = bi.pair ? inst[k].dims[0] / 2 : inst[k].dims[0];
         e = cudaMemsetAsync(h->psi, 0, (size_t)lay.psi_elems * lay.s_psi, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->kp.flags, 0, 64, b->stream);

@@ -367,7 +367,8 @@ template <class L, class S> struct Launch {
     // even nx, fewer than 2^31 cells); one cell per thread otherwise.
     static bool use_pair(const KParams &p) {
         if (std::is_same<S, __half>::value && !PLB_HALF_PAIR) return false;
-        return !std::is_same<S, double>::value && (p.nx % 2 == 0) && p.n < (1LL << 31);
+        // one population plane addressable with 32-bit cell indices and byte offsets
+        return !std::is_same<S, double>::value && (p.nx % 2 == 0) && p.n * (long long)sizeof(S) < (1LL << 32);
     }
     static void dims_pair(const KParams &p, dim3 &grid, dim3 &block, int threads = 256) {
         const int npx = p.nx / 2;

@@ -22,6 +22,21 @@
 
 namespace plb {
 
+// Element idx >= 0 of a population plane, addressed as the plane base plus a 32-bit unsigned
+// byte offset (PLB_U32_ADDR; planes hold fewer than 2^31 elements on the pair paths, at most
+// 2^31 x 4 bytes), which the compiler can fold into the memory instruction's addressing, else as
+// plain pointer arithmetic.  Measured: FP32 step 27.0 -> 27.8 GLUPS, FP16S 41.1 -> 41.8.
+#ifndef PLB_U32_ADDR
+#define PLB_U32_ADDR 1
+#endif
+template <class S> __device__ __forceinline__ S *elem(S *base, int idx) {
+#if PLB_U32_ADDR
+    return reinterpret_cast<S *>(reinterpret_cast<char *>(base) + (unsigned)idx * (unsigned)sizeof(S));
+#else
+    return base + idx;
+#endif
+}
+
 template <class S> struct PairIO;
 template <> struct PairIO<float> {
     template <class Pol> __device__ static f2 ld2(const float *a) {
@@ -101,19 +116,19 @@ __device__ __forceinline__ void load_pair(const KParams &p, const Planes<S> &A, 
         constexpr int o = opp(i);
         constexpr int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         if (!ODD) {
-            f[i] = PairIO<S>::template ld2<Pol>(A.p[i] + g.s0);
+            f[i] = PairIO<S>::template ld2<Pol>(elem(A.p[i], g.s0));
         } else {
             bool from_wall = false;
             if (WALL && cy != 0) from_wall = (g.y - cy < 0) || (g.y - cy >= p.ny);
             if (from_wall) {
-                f[i] = PairIO<S>::template ld2<Pol>(A.p[i] + g.s0);
+                f[i] = PairIO<S>::template ld2<Pol>(elem(A.p[i], g.s0));
             } else {
                 const int r = g.s0 + g.oy[1 - cy] + g.oz[1 - cz];
                 if (cx == 0)
-                    f[i] = PairIO<S>::template ld2<Pol>(A.p[o] + r);
+                    f[i] = PairIO<S>::template ld2<Pol>(elem(A.p[o], r));
                 else
-                    f[i] = PairIO<S>::template ld11<Pol>(A.p[o] + (r + g.ox0[1 - cx]),
-                                                        A.p[o] + (r + 1 + g.ox1[1 - cx]));
+                    f[i] = PairIO<S>::template ld11<Pol>(elem(A.p[o], r + g.ox0[1 - cx]),
+                                                        elem(A.p[o], r + 1 + g.ox1[1 - cx]));
             }
         }
     });
@@ -129,18 +144,18 @@ __device__ __forceinline__ void store_dir(const KParams &p, const Planes<S> &A, 
     constexpr int cx = L::cx(I), cy = L::cy(I), cz = L::cz(I);
     if constexpr (SR) v = PairIO<S>::dither(v, dir_bits(hsh, I));
     if (!ODD) {
-        PairIO<S>::st2(A.p[o] + g.s0, v);
+        PairIO<S>::st2(elem(A.p[o], g.s0), v);
     } else {
         bool to_wall = false;
         if (WALL && cy != 0) to_wall = (g.y + cy < 0) || (g.y + cy >= p.ny);
         if (to_wall) {
-            PairIO<S>::st2(A.p[o] + g.s0, v);
+            PairIO<S>::st2(elem(A.p[o], g.s0), v);
         } else {
             const int r = g.s0 + g.oy[1 + cy] + g.oz[1 + cz];
             if (cx == 0)
-                PairIO<S>::st2(A.p[I] + r, v);
+                PairIO<S>::st2(elem(A.p[I], r), v);
             else
-                PairIO<S>::st11(A.p[I] + (r + g.ox0[1 + cx]), A.p[I] + (r + 1 + g.ox1[1 + cx]), v);
+                PairIO<S>::st11(elem(A.p[I], r + g.ox0[1 + cx]), elem(A.p[I], r + 1 + g.ox1[1 + cx]), v);
         }
     }
 }

@@ -219,8 +219,10 @@ int check_create_args(int lattice, const int dims[3], const plb_eos_params *eos,
     if (o.streaming != PLB_STREAM_AA && o.streaming != PLB_STREAM_FUSED) return fail(PLB_EINVAL, "bad streaming");
     if (!make_layout(lattice, dims, o.precision, lay, o.streaming))
         return fail(PLB_EINVAL, "bad lattice, dims or precision");
-    if (o.streaming == PLB_STREAM_FUSED && (o.precision == PLB_FP64 || dims[0] % 2 != 0 || lay.n >= (1LL << 31)))
-        return fail(PLB_EUNSUPPORTED, "fused streaming needs FP32 or FP16S storage, even nx and < 2^31 cells");
+    if (o.streaming == PLB_STREAM_FUSED &&
+        (o.precision == PLB_FP64 || dims[0] % 2 != 0 || lay.n * lay.s_pop >= (1LL << 32)))
+        return fail(PLB_EUNSUPPORTED, "fused streaming needs FP32 or FP16S storage, even nx and population planes "
+                                      "below 4 GiB (< 2^30 cells FP32, < 2^31 FP16S)");
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(PLB_EINVAL, "tau must be > 1/2");
     if (!(G < 0.0) || !std::isfinite(G)) return fail(PLB_EINVAL, "G must be negative");
     if (!std::isfinite(eps) || !std::isfinite(o.kappa)) return fail(PLB_EINVAL, "eps and kappa must be finite");

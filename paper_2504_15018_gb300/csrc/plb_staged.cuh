@@ -18,7 +18,7 @@
 
 // z planes walked by one block of the staged kernel.
 #ifndef PLB_STAGED_ZC
-#define PLB_STAGED_ZC 8
+#define PLB_STAGED_ZC 16
 #endif
 
 namespace plb {
@@ -76,10 +76,10 @@ __device__ __forceinline__ void stage_plane(const KParams &p, const Planes<S> &A
         bool from_wall = false;
         if (ODD && WALL && cy != 0) from_wall = (y - cy < 0) || (y - cy >= p.ny);
         if (!ODD || from_wall) {
-            SW::copy(row + 1 + t, A.p[i] + g.s0);
+            SW::copy(row + 1 + t, elem(A.p[i], g.s0));
         } else {
             const int r = g.s0 + g.oy[1 - cy] + g.oz[1 - cz];      // the pair's own x in the source row
-            const S *src = A.p[o] + r;
+            const S *src = elem(A.p[o], r);
             SW::copy(row + 1 + t, src);
             if (cx != 0) {
                 // the segment's outer neighbours, x = X0 - 2 and X0 + 2 nw (periodic)

@@ -117,8 +117,8 @@ def test_laplace_surface_tension_matches_fp64(laplace_runs):
     once the per-step update is below half an FP16 ulp (stagnation), freezing the droplets
     before they relax, and the repeated rounding of near-steady values biases the mass
     (reported, not asserted).  The FP64 gamma is reported beside the diffusive-limit value of
-    App. A/B applied to the PR EOS (kappa = 1); at p_scale = 1 the interface is 1-2 cells wide,
-    so the gap is the O(dx^2) error of the coarse interface, not a failure."""
+    App. A/B applied to the PR EOS (kappa = 1): within 3 % (measured 2.1 %, 0.1 %, 1.2 % at
+    T/Tc = 0.7, 0.8, 0.9; at p_scale = 1 the interface is 1-2 cells wide)."""
     from oracle import params as pp
     a, b_, om = 2 / 49, 2 / 21, 0.327
     for t_ratio, (g64, rows64) in laplace_runs["fp64"].items():
@@ -128,7 +128,8 @@ def test_laplace_surface_tension_matches_fp64(laplace_runs):
         g_lim = pp.diffusive_gamma(lambda r: pp.pr_pressure(r, a, b_, 1.0, om, T), rv, rl, p0)
         print(f"T/Tc {t_ratio}: fp64 gamma {g64:.6f} (diffusive limit {g_lim:.6f}); spurious max|u| "
               f"{rows64[:, 4].max():.3e}")
-        assert 0.3 * g_lim < g64 < 3 * g_lim
+        # measured within 2.2 % of the diffusive-limit value at every temperature
+        assert abs(g64 / g_lim - 1) < 0.03
         # Laplace's law itself: the fit explains Delta P
         resid = rows64[:, 1] - (g64 / rows64[:, 0] + np.mean(rows64[:, 1] - g64 / rows64[:, 0]))
         assert np.max(np.abs(resid)) < 0.05 * np.max(np.abs(rows64[:, 1]))
@@ -196,7 +197,45 @@ def test_planar_coexistence_8x256_all_precisions():
     rv, rl, _ = pp.pr_maxwell(a, b_, 1.0, om, T)
     print(f"fp64 liquid {l64:.5f} vapour {v64:.5f}; mechanical stability {ml:.5f} {mv:.5f}; Maxwell {rl:.5f} {rv:.5f}")
     assert abs(l64 / ml - 1) < 0.01
-    assert abs(v64 - mv) < abs(v64 - rv)
+    # at s = 1 the interface is about one cell wide: the vapour sits 8.1 % above the
+    # mechanical-stability value (the oracle's diffusive ladder pins this gap and its
+    # second-order decay, tests/test_oracle_step.py); the FP64 GPU run is that same evaluation
+    assert 0.075 < v64 / mv - 1 < 0.087
+
+
+def test_planar_coexistence_ladder_fp64():
+    """Config 1 under diffusive refinement on the GPU (FP64): 8 x 256 2^k cells, p_EOS x 4^-k,
+    width 4 x 2^k, 20,000 x 4^k steps, k = 0, 1, 2.  The vapour density approaches the
+    mechanical-stability value of Sec. IV at each level's p_scale, and the Maxwell density, at
+    second order (the gaps fall by about 4 per level); the liquid stays within 0.1 %."""
+    import paper_2504_15018_gb300 as plb
+    from oracle import params as pp
+    a, b_, om = 2 / 49, 2 / 21, 0.327
+    T = 0.8 * pp.pr_Tc(a, b_)
+    rv, rl, _ = pp.pr_maxwell(a, b_, 1.0, om, T)
+    gaps, gaps_mx = [], []
+    for k in (0, 1, 2):
+        m = 2 ** k
+        dims = (8, 256 * m, 1)
+        rho = inputs.add_noise(inputs.slab(dims, 1, 64 * m, 192 * m, rl, rv, 4.0 * m), inputs.MASTER_SEED + 1, 1e-4)
+        lat = plb.Lattice(plb.PLB_D2Q9, dims, plb.pr_eos(0.8, p_scale=4.0 ** -k), 1.0, -1.0, 2.0,
+                          opts=plb.make_opts(precision=plb.PLB_FP64))
+        lat.init(rho)
+        lat.step(20000 * 4 ** k)
+        lat.status()
+        liq = lat.reduce(plb.PLB_MEAN_RHO, (0, 100 * m, 0), (8, 156 * m, 1))[0]
+        vap = 0.5 * (lat.reduce(plb.PLB_MEAN_RHO, (0, 0, 0), (8, 28 * m, 1))[0] +
+                     lat.reduce(plb.PLB_MEAN_RHO, (0, 228 * m, 0), (8, 256 * m, 1))[0])
+        ps = lambda r, s=4.0 ** -k: s * pp.pr_pressure(r, a, b_, 1.0, om, T)
+        mv, ml, _ = pp.mechanical_stability(ps, -1.0, 2.0, rho_max=0.999 / b_)
+        gaps.append(vap / mv - 1)
+        gaps_mx.append(vap / rv - 1)
+        print(f"k {k}: vapour {vap:.6f} (mechanical stability {mv:.6f}, Maxwell {rv:.6f}), liquid {liq:.6f} ({ml:.6f})")
+        assert abs(liq / ml - 1) < 1e-3
+    orders = [math.log2(gaps[i] / gaps[i + 1]) for i in range(2)]
+    orders_mx = [math.log2(gaps_mx[i] / gaps_mx[i + 1]) for i in range(2)]
+    print(f"gaps to mechanical stability {gaps} (orders {orders}); to Maxwell {gaps_mx} (orders {orders_mx})")
+    assert all(1.75 < o < 2.25 for o in orders + orders_mx)
 
 
 def _ladder(precision, levels, n0=64, steps0=1000, stochastic=0):
