@@ -12,8 +12,9 @@
 // Populations live in two copies: the kernel reads A (natural layout, f_i(x) at A[i][x]) and
 // pushes the post-collision populations into B (B[i][x + c_i], halfway bounce-back at the y
 // walls), so no block can read a population another block has already overwritten.  The
-// per-cell arithmetic (psi_pair_of, force_pair_from, collide_store_pair) is the same code as the
-// two-pass kernels, so both give the same populations bit for bit.
+// per-cell arithmetic (psi_pair_of, force_pair_from, collide_store_pair) is the code of the
+// two-pass kernels; with the same collision form (always for D2Q9 and FP16 storage) both give
+// the same populations bit for bit.
 #pragma once
 #include "plb_pair.cuh"
 
@@ -21,15 +22,44 @@
 #define PLB_FUSED_PSI_POL LdKeep
 #endif
 
+// Collision form of the single pass: 1 the moment-space D3Q19 collision for every storage
+// precision (FP32 single pass on the D3Q19 plates workload: 27.3 -> 29.1 GLUPS; its populations
+// then differ from the two-pass FP32 kernels, which keep the per-pair form, by rounding), -1 the
+// form of the two-pass kernels (bit-identical to them).
+#ifndef PLB_FUSED_MOMENT
+#define PLB_FUSED_MOMENT 1
+#endif
+
 namespace plb {
 
-template <class L> struct FusedTile {
+// v in [-n, 2n) wrapped into [0, n); any v for lattices narrower than a tile.
+__device__ __forceinline__ int wrap_near(int v, int n) {
+    if (v < 0) v += n;
+    else if (v >= n) v -= n;
+    if ((unsigned)v >= (unsigned)n) v = ((v % n) + n) % n;
+    return v;
+}
+
+// Tile rows (FP32 and FP16 storage) and threads per block of the single pass (two blocks of 256
+// threads per SM at the 128-register cap).  D3Q19 plates workload, GLUPS with 8 / 16 / 32 rows:
+// FP32 27.9 / 29.0 / 26.6, FP16S 31.7 / 34.3 / 36.2.
+#ifndef PLB_FUSED_TY
+#define PLB_FUSED_TY 16
+#endif
+#ifndef PLB_FUSED_TY_HALF
+#define PLB_FUSED_TY_HALF 32
+#endif
+#ifndef PLB_FUSED_THREADS
+#define PLB_FUSED_THREADS 256
+#endif
+
+template <class L, class S> struct FusedTile {
     static constexpr int TX = 64;                      // cells in x (32 pairs)
-    static constexpr int TY = 16;                      // rows
+    static constexpr int TY = sizeof(S) == 2 ? PLB_FUSED_TY_HALF : PLB_FUSED_TY;   // rows
     static constexpr int HP = TX / 2 + 2;              // pairs per shared row: one halo pair each side
     static constexpr int RY = TY + 2;                  // rows with the halo
     static constexpr int NPL = L::D == 3 ? 3 : 1;      // psi planes in the ring
-    static constexpr int THREADS = 256;
+    static constexpr int THREADS = PLB_FUSED_THREADS;
 };
 
 // psi of the halo-extended tile of plane zg (any integer: wrapped) into ring plane `plane`.
@@ -37,8 +67,8 @@ template <class L> struct FusedTile {
 template <class L, class S>
 __device__ __forceinline__ void fused_psi_plane(const KParams &p, const Planes<S> &A, float *plane, int x0, int y0,
                                                 int zg) {
-    using Tl = FusedTile<L>;
-    const int z = ((zg % p.nz) + p.nz) % p.nz;
+    using Tl = FusedTile<L, S>;
+    const int z = wrap_near(zg, p.nz);
     for (int k = threadIdx.x; k < Tl::RY * Tl::HP; k += Tl::THREADS) {
         const int ly = k / Tl::HP, hp = k - ly * Tl::HP;
         int y = y0 - 1 + ly;
@@ -53,9 +83,9 @@ __device__ __forceinline__ void fused_psi_plane(const KParams &p, const Planes<S
             // the halo of a ragged tile are clamped (computed, never read)
             y = y < 0 ? 0 : (y >= p.ny ? p.ny - 1 : y);
         } else {
-            y = ((y % p.ny) + p.ny) % p.ny;
+            y = wrap_near(y, p.ny);
         }
-        const int x = (((x0 - 2 + 2 * hp) % p.nx) + p.nx) % p.nx;     // even: nx is even
+        const int x = wrap_near(x0 - 2 + 2 * hp, p.nx);     // even: nx is even
         const int s0 = x + p.nx * (y + p.ny * z);
         f2 f[L::Q];
         Unroll<0, L::Q>::run([&](auto ic) {
@@ -75,7 +105,7 @@ template <class L, class S, int MRT, bool SR>
 __device__ __forceinline__ void fused_collide_plane(const KParams &p, const Planes<S> &A, const Planes<S> &B,
                                                     const float *pm, const float *pc, const float *pp, int x0,
                                                     int y0, int z, unsigned salt) {
-    using Tl = FusedTile<L>;
+    using Tl = FusedTile<L, S>;
     constexpr int NP = Tl::TX / 2;
     constexpr int row = 2 * Tl::HP;
     for (int k = threadIdx.x; k < Tl::TY * NP; k += Tl::THREADS) {
@@ -99,16 +129,16 @@ __device__ __forceinline__ void fused_collide_plane(const KParams &p, const Plan
         force_pair_from<L>(p, at, F);
         // push streaming into B: the odd-parity store of the two-pass kernels
         if (p.wall_y && (y == 0 || y == p.ny - 1))
-            collide_store_pair<L, S, MRT, true, true, SR>(p, B, g, f, F, salt);
+            collide_store_pair<L, S, MRT, true, true, SR, PLB_FUSED_MOMENT>(p, B, g, f, F, salt);
         else
-            collide_store_pair<L, S, MRT, true, false, SR>(p, B, g, f, F, salt);
+            collide_store_pair<L, S, MRT, true, false, SR, PLB_FUSED_MOMENT>(p, B, g, f, F, salt);
     }
 }
 
 // Grid: (ceil(nx / TX), ceil(ny / TY), ceil(nz / zc)); block: THREADS threads.
 template <class L, class S, int MRT, bool SR>
-__global__ void __launch_bounds__(256, 2) k_fused_pair(KParams p, Planes<S> A, Planes<S> B, int zc) {
-    using Tl = FusedTile<L>;
+__global__ void __launch_bounds__(PLB_FUSED_THREADS, 512 / PLB_FUSED_THREADS) k_fused_pair(KParams p, Planes<S> A, Planes<S> B, int zc) {
+    using Tl = FusedTile<L, S>;
     constexpr int PLANE = Tl::RY * 2 * Tl::HP;
     __shared__ __align__(16) float ring[Tl::NPL * PLANE];
     const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY;

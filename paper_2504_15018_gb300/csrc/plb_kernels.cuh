@@ -424,20 +424,21 @@ template <class L, class S> struct Launch {
     template <int MRT, bool ODD> static void collide_t(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         dim3 grid, block;
         if constexpr (!std::is_same<S, double>::value) {
-            if (use_pair(p) && std::is_same<L, D3Q19>::value &&
-                (std::is_same<S, __half>::value ? PLB_STAGED_HALF : PLB_STAGED_FLOAT) != 0) {
-                constexpr int per = 2 * StagedShape<L>::THREADS;
-                const dim3 sgrid((p.nx + per - 1) / per, p.ny, (p.nzl + PLB_STAGED_ZC - 1) / PLB_STAGED_ZC);
-                const dim3 sblock(StagedShape<L>::THREADS);
-                if constexpr (Store<S>::SHIFT) {
-                    if (p.stochastic) {
-                        k_collide_staged<L, S, MRT, ODD, true><<<sgrid, sblock, 0, st>>>(p, planes(p, A),
-                                                                                         (const float *)psi);
-                        return;
+            if constexpr (std::is_same<L, D3Q19>::value) {
+                if (use_pair(p) && (std::is_same<S, __half>::value ? PLB_STAGED_HALF : PLB_STAGED_FLOAT) != 0) {
+                    constexpr int per = 2 * StagedShape<L>::THREADS;
+                    const dim3 sgrid((p.nx + per - 1) / per, p.ny, (p.nzl + PLB_STAGED_ZC - 1) / PLB_STAGED_ZC);
+                    const dim3 sblock(StagedShape<L>::THREADS);
+                    if constexpr (Store<S>::SHIFT) {
+                        if (p.stochastic) {
+                            k_collide_staged<L, S, MRT, ODD, true><<<sgrid, sblock, 0, st>>>(p, planes(p, A),
+                                                                                             (const float *)psi);
+                            return;
+                        }
                     }
+                    k_collide_staged<L, S, MRT, ODD, false><<<sgrid, sblock, 0, st>>>(p, planes(p, A), (const float *)psi);
+                    return;
                 }
-                k_collide_staged<L, S, MRT, ODD, false><<<sgrid, sblock, 0, st>>>(p, planes(p, A), (const float *)psi);
-                return;
             }
             if (use_pair(p)) {
                 dims_pair(p, grid, block, PLB_PAIR_THREADS);
@@ -511,19 +512,47 @@ template <class L, class S> struct Launch {
     static void rebalance(const KParams &p, void *A, const void *psi, cudaStream_t st) {
         k_rebalance<L, S><<<blocks(p.n, 256), 256, 0, st>>>(p, (S *)A, (const PsiT *)psi);
     }
-    // single pass: tiles of 64 x 16 cells, each block walking a chunk of zc planes; zc gives
-    // about 1200 blocks (four waves of two blocks on 152 SMs), at least 4 planes per chunk
+    // resident blocks per SM of the single-pass kernel
+    template <int MRT> static int fused_blocks_per_sm() {
+        static int nb = 0;
+        if (nb == 0) {
+            int v = 0;
+            if constexpr (!std::is_same<S, double>::value) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fused_pair<L, S, MRT, false>,
+                                                                  FusedTile<L, S>::THREADS, 0) != cudaSuccess || v < 1)
+                    v = 1;
+            }
+            nb = v < 1 ? 1 : v;
+        }
+        return nb;
+    }
+    // single pass: tiles of 64 x 16 (FP32) or 64 x 32 (FP16) cells, each block walking a chunk
+    // of zc planes.  The chunk
+    // count minimises (waves of resident blocks) x (planes per chunk + 0.5): a block also forms
+    // psi of the two planes before its chunk, at about a third of a collided plane's cost each,
+    // and the last wave of a grid that is not a multiple of the resident blocks runs partly idle.
     template <int MRT> static void fused_t(const KParams &p, const void *A, void *B, cudaStream_t st) {
         if constexpr (!std::is_same<S, double>::value) {
-            using Tl = FusedTile<L>;
+            using Tl = FusedTile<L, S>;
             const int gx = (p.nx + Tl::TX - 1) / Tl::TX, gy = (p.ny + Tl::TY - 1) / Tl::TY;
             int zc = 1, gz = 1;
             if (L::D == 3) {
-                const long long want = (1200 + (long long)gx * gy - 1) / ((long long)gx * gy);
-                zc = (int)((p.nz + want - 1) / want);
-                if (zc < 4) zc = 4;
-                if (zc > p.nz) zc = p.nz;
-                gz = (p.nz + zc - 1) / zc;
+                const long long tiles = (long long)gx * gy;
+                const long long resident = (long long)fused_blocks_per_sm<MRT>() * sm_count();
+                double best = 0.0;
+                const int gmax = p.nz < 4096 ? p.nz : 4096;
+                for (int g = 1; g <= gmax; ++g) {
+                    const int zcg = (p.nz + g - 1) / g;
+                    const int gzg = (p.nz + zcg - 1) / zcg;
+                    if (gzg != g) continue;                       // the same chunking as a smaller g
+                    const long long waves = (tiles * gzg + resident - 1) / resident;
+                    const double cost = (double)waves * (zcg + 0.5);
+                    if (g == 1 || cost < best) {
+                        best = cost;
+                        zc = zcg;
+                        gz = gzg;
+                    }
+                }
             }
             const dim3 grid(gx, gy, gz), block(Tl::THREADS);
             if constexpr (Store<S>::SHIFT) {

@@ -166,12 +166,14 @@ template <class L, class S> struct UseMomentCollide {
         std::is_same<L, D3Q19>::value && (PLB_MOMENT_COLLIDE == 2 || (PLB_MOMENT_COLLIDE == 1 && Store<S>::SHIFT));
 };
 
-template <class L, class S, int MRT, bool ODD, bool WALL, bool SR>
+// MOM: -1 the collision form of UseMomentCollide, 0 per pair, 1 moment space (D3Q19).
+template <class L, class S, int MRT, bool ODD, bool WALL, bool SR, int MOM = -1>
 __device__ __forceinline__ void collide_store_pair(const KParams &p, const Planes<S> &A, const GeoPair &g, f2 *f,
                                                    const f2 F[3], unsigned salt) {
     const unsigned hsh = SR ? cell_hash((unsigned)g.s0 + p.cell_base, salt) : 0u;
     auto emit = [&](auto ic, const f2 &v) { store_dir<L, S, ODD, WALL, SR, decltype(ic)::value>(p, A, g, v, hsh); };
-    if constexpr (UseMomentCollide<L, S>::value)
+    constexpr bool moment = MOM < 0 ? UseMomentCollide<L, S>::value : (MOM > 0 && std::is_same<L, D3Q19>::value);
+    if constexpr (moment)
         collide_moments_d3q19<MRT, Store<S>::SHIFT, f2>(p, f, F, emit);
     else
         collide_emit<L, MRT, Store<S>::SHIFT, f2>(p, f, F, emit);
@@ -430,8 +432,11 @@ __device__ __forceinline__ void psi_quad_body(const KParams &p, const Planes<__h
     if (by || bz || x0 + 3 == p.nx - 1) psi_ghosts<L>(p, psi, x0 + 3, y, z, v23.v.y);
 }
 
+// Blocks of 256 threads with an explicit minimum of one resident block per SM: the register
+// allocator then keeps more loads in flight per thread (54 / 72 registers for even / odd steps
+// against 32 / 44 with the thread count alone), measured 92.9 -> 94.2 % of the copy bandwidth.
 template <class L, bool ODD>
-__global__ void __launch_bounds__(256) k_psi_quad(KParams p, Planes<__half> A, float *__restrict__ psi) {
+__global__ void __launch_bounds__(256, 1) k_psi_quad(KParams p, Planes<__half> A, float *__restrict__ psi) {
     const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x), y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;
     const int z = blockIdx.z + p.z0;
