@@ -539,20 +539,30 @@ template <class L, class S> struct Launch {
             if (L::D == 3) {
                 const long long tiles = (long long)gx * gy;
                 const long long resident = (long long)fused_blocks_per_sm<MRT>() * sm_count();
-                double best = 0.0;
-                const int gmax = p.nz < 4096 ? p.nz : 4096;
-                for (int g = 1; g <= gmax; ++g) {
-                    const int zcg = (p.nz + g - 1) / g;
-                    const int gzg = (p.nz + zcg - 1) / zcg;
-                    if (gzg != g) continue;                       // the same chunking as a smaller g
-                    const long long waves = (tiles * gzg + resident - 1) / resident;
-                    const double cost = (double)waves * (zcg + 0.5);
-                    if (g == 1 || cost < best) {
-                        best = cost;
-                        zc = zcg;
-                        gz = gzg;
+                // the last search's result (one lattice stepped many times asks the same again)
+                static thread_local long long key[3] = {-1, -1, -1};
+                static thread_local int last[2] = {1, 1};
+                if (key[0] != tiles || key[1] != resident || key[2] != p.nz) {
+                    double best = 0.0;
+                    const int gmax = p.nz < 4096 ? p.nz : 4096;
+                    for (int g = 1; g <= gmax; ++g) {
+                        const int zcg = (p.nz + g - 1) / g;
+                        const int gzg = (p.nz + zcg - 1) / zcg;
+                        if (gzg != g) continue;                       // the same chunking as a smaller g
+                        const long long waves = (tiles * gzg + resident - 1) / resident;
+                        const double cost = (double)waves * (zcg + 0.5);
+                        if (g == 1 || cost < best) {
+                            best = cost;
+                            last[0] = zcg;
+                            last[1] = gzg;
+                        }
                     }
+                    key[0] = tiles;
+                    key[1] = resident;
+                    key[2] = p.nz;
                 }
+                zc = last[0];
+                gz = last[1];
             }
             const dim3 grid(gx, gy, gz), block(Tl::THREADS);
             if constexpr (Store<S>::SHIFT) {
