@@ -29,6 +29,12 @@ CASES = {
                                   precision=2),
     "d3q19_fp16s_sr_mrt_walls": dict(lattice=1, dims=(34, 18, 12), wall=True, shape="slab", mrt=True, rates=RATES,
                                      precision=2, fp16_rounding=1),
+    # nx / 4 a multiple of 32 and several row segments: whole warps of the four-cell FP16 psi
+    # pass and of the staged kernel along x
+    "d3q19_fp16s_mrt_walls_wide": dict(lattice=1, dims=(256, 18, 6), wall=True, shape="slab", mrt=True,
+                                       rates=RATES, precision=2),
+    "d3q19_fp16s_sr_bgk_wide": dict(lattice=1, dims=(128, 20, 5), u0=(0.02, -0.01, 0.015), precision=2,
+                                    fp16_rounding=1),
     "d2q9_fp16s_bgk_droplet": dict(lattice=0, dims=(80, 70, 1), precision=2),
     "d3q19_fp32_mrt_wetting_walls": dict(lattice=1, dims=(24, 20, 10), wall=True, shape="slab", mrt=True,
                                          rates=RATES, wall_rho=0.9, precision=1),
