@@ -56,6 +56,10 @@ def parse_args():
                     help="plates: D3Q19 512x256x256 two-phase plates; batch96: 96 uneven D2Q9 instances")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-plan", action="store_true",
+                    help="time the FP64 oracle alone on the host cores: D2Q9 BGK 256^2, D3Q19 BGK and MRT 96^3, "
+                         "1 thread and all cores, median of 3 (prints one JSON line, no GPU work)")
+    ap.add_argument("--cpu-plan-child", default="", help=argparse.SUPPRESS)
     ap.add_argument("--e2e-steps", type=int, default=100,
                     help="steps of the end-to-end run (init from host, steps, fields back to host)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -393,6 +397,64 @@ def cpu_baseline_sample(args, seconds=12.0):
                       f"plates workload (walls in y), {steps} steps, {dt:.1f} s, OpenMP over cells"}
 
 
+# workload, lattice (0 D2Q9, 1 D3Q19), dims, MRT, steps with 1 thread, steps with all cores
+CPU_PLAN = (("d2q9_bgk_256x256_droplet", 0, (256, 256, 1), False, 200, 2000),
+            ("d3q19_bgk_96x96x96_droplet", 1, (96, 96, 96), False, 10, 100),
+            ("d3q19_mrt_96x96x96_droplet", 1, (96, 96, 96), True, 10, 100))
+
+
+def cpu_plan_child(spec):
+    """One entry of the CPU plan in this process (OMP_NUM_THREADS set by the parent): three timed
+    runs of the oracle after one warm-up step; prints their MLUPS."""
+    import oracle
+    from oracle import params as pp
+    from paper_2504_15018_gb300 import inputs
+    name, steps = spec.rsplit(":", 1)
+    steps = int(steps)
+    _, lattice, dims, mrt, _, _ = next(e for e in CPU_PLAN if e[0] == name)
+    a, b, om = 2.0 / 49.0, 2.0 / 21.0, 0.327
+    T = T_RATIO * pp.pr_Tc(a, b)
+    rv, rl, _ = pp.pr_maxwell(a, b, 1.0, om, T)
+    nd = 2 if lattice == 0 else 3
+    center = tuple(d / 2 - 0.3 for d in dims[:nd])
+    rho = inputs.droplet(dims, center, dims[0] / 4, rv, rl, 4.0)
+    P = oracle.make_params(oracle.D2Q9 if lattice == 0 else oracle.D3Q19, dims,
+                           eos=dict(kind="pr", a=a, b=b, R=1.0, omega=om, T=T), tau=1.0, mrt=mrt, rates=MRT_RATES)
+    f = oracle.run(P, oracle.init(P, rho), 1)
+    n = dims[0] * dims[1] * dims[2]
+    out = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        f = oracle.run(P, f, steps)
+        out.append(n * steps / (time.perf_counter() - t0) / 1e6)
+    print(json.dumps({"mlups": out}))
+
+
+def run_cpu_plan(args):
+    """The FP64 oracle on the host cores, 1 thread and all cores (one child process each, so
+    OpenMP starts with that thread count); median of 3 runs."""
+    ncores = os.cpu_count() or 1
+    cpu = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    rows = []
+    for name, _, dims, _, s1, sn in CPU_PLAN:
+        for threads, steps in ((1, s1), (ncores, sn)):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-plan-child", f"{name}:{steps}"],
+                               env=env, capture_output=True, text=True, check=True)
+            mlups = json.loads(r.stdout.strip().splitlines()[-1])["mlups"]
+            rows.append({"workload": name, "threads": threads, "steps": steps,
+                         "mlups_median": round(float(np.median(mlups)), 3), "runs": [round(v, 3) for v in mlups]})
+    print(json.dumps({"cpu_plan": rows, "kind": "oracle (plain FP64 C, OpenMP over cells)", "cores": ncores,
+                      "cpu": cpu}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -517,7 +579,11 @@ def run_batch(args):
 
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.cpu_plan_child:
+        cpu_plan_child(args.cpu_plan_child)
+    elif args.cpu_plan:
+        run_cpu_plan(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch96":
         run_batch(args)

@@ -1,5 +1,6 @@
 """bench.py's roofline bookkeeping: the algorithmic bytes per cell update of each kernel and
-step, and the DRAM traffic it reports only for the kernel sources the counters were taken on."""
+step, the DRAM traffic it reports only for the kernel sources the counters were taken on, and
+the CPU-baseline plan entry."""
 import os
 import sys
 
@@ -45,3 +46,16 @@ def test_traffic_is_reported_only_for_the_recorded_sources(tmp_path, monkeypatch
     assert bench.recorded_traffic("wl_b", "k_collide_pair") is None
     (tmp_path / "profiles" / "roofline_traffic.md").write_text("kernel_source_sha: 0123456789abcdef\n\n" + table)
     assert bench.recorded_traffic("wl_a", "k_collide_pair") is None
+
+
+def test_cpu_plan_entry_times_the_oracle_in_a_child_process():
+    """One entry of the CPU-baseline plan (the oracle alone, thread count from OMP_NUM_THREADS)
+    runs in its own process and reports three positive rates."""
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-plan-child", "d2q9_bgk_256x256_droplet:2"],
+                       env=env, capture_output=True, text=True, check=True, timeout=300)
+    mlups = json.loads(r.stdout.strip().splitlines()[-1])["mlups"]
+    assert len(mlups) == 3 and all(v > 0 for v in mlups)
