@@ -525,6 +525,9 @@ def run_batch(args):
         b.init(k, rho, u0)
     tile, bps, _ = b.autotune(3)
     b.step(max(args.warmup, 3))
+    # one untimed call with the timed step count: plb_batch_step captures and instantiates a
+    # CUDA graph for each new step count, which must not fall inside the timed region
+    b.step(args.steps)
     b.status()
     st = b.stream
     torch.cuda.synchronize()
@@ -561,7 +564,7 @@ def run_batch(args):
     sep_glups = cells * nsep / t_sep / 1e9
     del lats
     line = {"metric": METRIC, "value": round(value, 4), "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "warmup": max(args.warmup, 3) + args.steps, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic (seeded)",
             "config": {"workload": f"d2q9_batch96_uneven_{prec}_{args.collision}", "instances": len(insts),
                        "cells": cells, "sides": sorted({d['side'] for d in desc}),
