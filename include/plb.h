@@ -110,7 +110,10 @@ typedef struct plb_opts {
                                 the populations (twice the population memory, about 30 % fewer DRAM
                                 bytes per step); PLB_FP32 / PLB_FP16S with even nx and population
                                 planes below 4 GiB (fewer than 2^30 / 2^31 cells) only, not in
-                                batches [PLB_STREAM_AA].  Both give the same populations. */
+                                batches [PLB_STREAM_AA].  Both give the same populations bit for
+                                bit, except D3Q19 with PLB_FP32 storage, where the single pass
+                                collides in moment space and the two-pass kernels population pair
+                                by population pair: there they agree to FP32 rounding. */
     double wall_rho;         /* wall_y = 1 only: > 0 makes the walls wetting walls, whose nodes carry
                                 the pseudo-potential psi(wall_rho) of a prescribed wall density
                                 instead of mirroring the adjacent fluid row; wall_rho near rho_l
